@@ -316,3 +316,20 @@ def test_code_construction_properties():
             for a, b in itertools.combinations(cols, 2):
                 assert (a, b) not in pairs
                 pairs.add((a, b))
+
+
+def test_vnp_saturates_at_255(oracle_lib):
+    """A hand-worked binary case where the variable-node cap decides a symbol.
+
+    H = [[1,1,0],[1,0,1]]; v0 leans to 0 by 255, v1 to 1 by 255, v2 to 0 by 255.
+    Iteration 1: v0 receives +255 from check 1 and -255 from check 0, so its
+    message to check 0 is 255 + 255 = 510, capped to 255.  Iteration 2:
+    check 0 forwards that 255 to v1, whose posterior is then 255 - 255 = 0 in
+    LLR, a tie, decided as the lowest symbol, 0.  A cap of 254 would give 1.
+    """
+    code = I.code_from_dense(np.array([[1, 1, 0], [1, 0, 1]]), 2, 0x3)
+    gamma = np.array([[[0, 255], [255, 0], [0, 255]]], np.uint8)
+    sym, its, ok = oracle_lib.decode(code, gamma, 2, 0)
+    assert sym.tolist() == [[0, 0, 0]] and its.tolist() == [2] and ok.tolist() == [1]
+    ws, wi, wo = binary_min_sum(code, gamma, 2, 0)
+    assert np.array_equal(sym, ws)
