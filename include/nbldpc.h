@@ -1,0 +1,153 @@
+/*
+ * nbldpc.h -- min-max (MMA) decoding of non-binary LDPC codes over GF(2^p)
+ * on NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * The operation is Alg. 2 of "In-Memory Non-Binary LDPC Decoding"
+ * (arXiv 2508.03567): flooding belief propagation with the min-max check-node
+ * rule computed by forward/backward (F, B) matrices, variable-node sums with
+ * min-normalization, an a-posteriori argmin decision and a syndrome test that
+ * stops each frame early.  Messages are 8-bit unsigned integers; the only
+ * saturation is min(255, .) after the variable-node normalization.
+ *
+ * Conventions shared by every entry point
+ *  - Field: q = 2^p, 2 <= q <= 256.  Elements are the integers 0..q-1 in
+ *    polynomial basis (bit i = coefficient of x^i); the primitive element is
+ *    x = 2 (Sec. 2.1).
+ *  - Reliabilities gamma[f][n][a] (uint8) are the initial LLR-like metrics of
+ *    Alg. 2 (gamma_n(a) = ln(p(eta)/p(a)), quantized): smaller is more likely.
+ *    Index a is the symbol value.  They are used as given (no renormalization).
+ *  - Hard decisions take the lowest symbol on ties.  The stop test on the
+ *    decision of iteration k-1 runs before iteration k; out_iters counts the
+ *    completed check+variable passes (0 when the channel decision already
+ *    satisfies every check and early_stop is set).
+ *  - Every status is one of the NBLDPC_* codes below; nbldpc_status_string()
+ *    describes it.  Errors detected on the host are returned before any GPU
+ *    work is queued and leave the outputs untouched.
+ */
+#ifndef NBLDPC_H
+#define NBLDPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbldpc_code nbldpc_code; /* opaque; immutable after create */
+
+enum {
+  NBLDPC_OK = 0,
+  NBLDPC_ERR_ARG = -1,         /* null pointer, negative count, short workspace ... */
+  NBLDPC_ERR_POLY = -2,        /* q not a power of two in [2,256] or polynomial not primitive of degree p */
+  NBLDPC_ERR_H = -3,           /* malformed parity-check matrix */
+  NBLDPC_ERR_CUDA = -4,        /* a CUDA call failed (also reports earlier asynchronous faults) */
+  NBLDPC_ERR_NOMEM = -5,       /* device or host allocation failed inside nbldpc_code_create */
+  NBLDPC_ERR_TIMEOUT = -6,     /* reserved: a bounded device-side wait expired */
+  NBLDPC_ERR_UNSUPPORTED = -7  /* valid code outside this build's limits (see nbldpc_code_create) */
+};
+
+/*
+ * Build a code handle from H given as CSR rows (Sec. 2.1: M x N sparse
+ * parity-check matrix over GF(q); Tanner graph with M check and N variable
+ * nodes; edge = non-zero entry).
+ *
+ *   q         field order, a power of two in [2, 256]
+ *   prim_poly primitive polynomial including the x^p term (e.g. 0x11D for q = 256)
+ *   n_cols    N, number of variable nodes (symbols per frame)
+ *   n_rows    M, number of check nodes
+ *   row_ptr   host, [n_rows+1], row_ptr[0] = 0, non-decreasing; nnz = row_ptr[n_rows]
+ *   col_idx   host, [nnz], 0 <= col < n_cols, no column twice within a row
+ *   coef      host, [nnz], 1 <= coef < q (the GF coefficient h_{m,n})
+ *   out       receives the handle; set to NULL on failure
+ *
+ * Checks: every row has degree >= 2, every column degree >= 1.  Build limits
+ * (NBLDPC_ERR_UNSUPPORTED beyond them): n_cols < 65535, nnz < 65535, row
+ * degree <= 64, column degree <= 64.  The edge order within a row does not
+ * change any output (the min-max convolution is commutative and associative).
+ *
+ * The handle owns device copies of H, its variable-node view and the GF
+ * exponent/logarithm tables, allocated on the device that is current at this
+ * call; decode on that device.  Copies the host arrays; the caller keeps
+ * ownership of them.  Thread safe for concurrent decodes that use distinct
+ * workspaces.
+ */
+int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const int32_t *row_ptr,
+                       const int32_t *col_idx, const uint8_t *coef, nbldpc_code **out);
+
+/* Free a handle (NULL is accepted).  No decode on it may be in flight. */
+void nbldpc_code_destroy(nbldpc_code *code);
+
+/* Shape of a handle; any output pointer may be NULL. */
+int nbldpc_code_info(const nbldpc_code *code, int *q, int *n, int *m, int *nnz);
+
+/*
+ * Device workspace nbldpc_decode needs for `frames` frames, in bytes (a
+ * persistent grid sized to the current device keeps one message slot of
+ * nnz*q bytes per resident block, so the size saturates for large batches).
+ */
+int nbldpc_decode_workspace_size(const nbldpc_code *code, int frames, size_t *bytes);
+
+/*
+ * Decode `frames` frames (Alg. 2), stream-ordered on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Returns after queueing.
+ *
+ *   gamma_dev      device, [frames][n_cols][q] uint8, read only
+ *   max_iters      I_max >= 0 (0: channel decision only)
+ *   early_stop     non-zero: stop a frame once its decision satisfies every check
+ *   out_sym_dev    device, [frames][n_cols] uint8: decided symbols
+ *   out_iters_dev  device, [frames] int32: iterations run
+ *   out_ok_dev     device, [frames] uint8: 1 if the returned symbols satisfy every check
+ *   workspace_dev  device, >= nbldpc_decode_workspace_size(code, frames) bytes,
+ *                  16-byte aligned; scratch owned by the caller, contents
+ *                  undefined after the call; one decode at a time per workspace
+ *
+ * All device buffers are owned by the caller and must stay valid until the
+ * queued work completes.  frames == 0 queues nothing.  Each frame's outputs
+ * depend only on that frame's gamma (not on the batch it is decoded in).
+ */
+int nbldpc_decode(const nbldpc_code *code, const uint8_t *gamma_dev, int frames, int max_iters,
+                  int early_stop, uint8_t *out_sym_dev, int32_t *out_iters_dev, uint8_t *out_ok_dev,
+                  void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * Device workspace nbldpc_decode_host needs when it streams the batch in
+ * chunks of `chunk_frames` frames (two chunks in flight).
+ */
+int nbldpc_decode_host_workspace_size(const nbldpc_code *code, int chunk_frames, size_t *bytes);
+
+/*
+ * Same decode as nbldpc_decode, from and to HOST buffers: the batch is moved
+ * in chunks of `chunk_frames` frames, the host-to-device copy of the next
+ * chunk and the device-to-host copy of the previous one overlapping the
+ * decode of the current chunk.  Pinned (page-locked) host buffers give
+ * asynchronous copies; pageable ones work but serialize.
+ *
+ *   gamma_host     host, [frames][n_cols][q] uint8
+ *   out_*_host     host, as in nbldpc_decode
+ *   chunk_frames   frames per chunk (> 0)
+ *   workspace_dev  device, >= nbldpc_decode_host_workspace_size(code, chunk_frames)
+ *
+ * Stream-ordered on `cuda_stream`: the host outputs are complete once that
+ * stream has been synchronized.  Host and workspace buffers must stay valid
+ * until then.
+ */
+int nbldpc_decode_host(const nbldpc_code *code, const uint8_t *gamma_host, int frames, int max_iters,
+                       int early_stop, uint8_t *out_sym_host, int32_t *out_iters_host,
+                       uint8_t *out_ok_host, int chunk_frames, void *workspace_dev,
+                       size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * Number of decode-kernel launches the calls above queued since the library
+ * was loaded (all threads, all handles).  Launch accounting for benchmarks.
+ */
+uint64_t nbldpc_kernel_launch_count(void);
+
+/* Static description of a status code (never NULL). */
+const char *nbldpc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBLDPC_H */

@@ -1,0 +1,207 @@
+"""Python binding of the C ABI in include/nbldpc.h (argument marshalling only).
+
+Functions carry the C names.  Device buffers are torch CUDA tensors (PyTorch
+supplies memory and streams); every decode step runs in the library's CUDA
+kernels.  There is no CPU fallback: if libnbldpc.so is missing or cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnbldpc.so")
+
+NBLDPC_OK = 0
+NBLDPC_ERR_ARG = -1
+NBLDPC_ERR_POLY = -2
+NBLDPC_ERR_H = -3
+NBLDPC_ERR_CUDA = -4
+NBLDPC_ERR_NOMEM = -5
+NBLDPC_ERR_TIMEOUT = -6
+NBLDPC_ERR_UNSUPPORTED = -7
+
+EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
+            "nbldpc_decode_workspace_size", "nbldpc_decode", "nbldpc_decode_host_workspace_size",
+            "nbldpc_decode_host", "nbldpc_kernel_launch_count", "nbldpc_status_string")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class NbldpcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {nbldpc_status_string(status)} ({status})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnbldpc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA decoder library not built: {LIB_PATH} is missing "
+                                   "(run paper_2508_03567_gb300.build.build_library())")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, sz = ctypes.c_void_p, ctypes.c_size_t
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.nbldpc_code_create.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                             i32p, i32p, ctypes.POINTER(ctypes.c_uint8),
+                                             ctypes.POINTER(vp)]
+            L.nbldpc_code_destroy.argtypes = [vp]
+            L.nbldpc_code_destroy.restype = None
+            L.nbldpc_code_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
+            L.nbldpc_decode_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_decode.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                        vp, sz, vp]
+            L.nbldpc_decode_host_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_decode_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                             vp, ctypes.c_int, vp, sz, vp]
+            L.nbldpc_kernel_launch_count.argtypes = []
+            L.nbldpc_kernel_launch_count.restype = ctypes.c_uint64
+            L.nbldpc_status_string.argtypes = [ctypes.c_int]
+            L.nbldpc_status_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str) -> None:
+    if st != NBLDPC_OK:
+        raise NbldpcError(st, what)
+
+
+def nbldpc_status_string(status: int) -> str:
+    return lib().nbldpc_status_string(int(status)).decode()
+
+
+def nbldpc_kernel_launch_count() -> int:
+    return int(lib().nbldpc_kernel_launch_count())
+
+
+def nbldpc_code_create(q: int, prim_poly: int, n_cols: int, n_rows: int, row_ptr, col_idx, coef) -> int:
+    """Handle (int) for H in CSR form; raises NbldpcError on a rejected code."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    cf = np.ascontiguousarray(coef, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    st = lib().nbldpc_code_create(int(q), int(prim_poly), int(n_cols), int(n_rows),
+                                  rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  cf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(h))
+    _check(st, "nbldpc_code_create")
+    return h.value
+
+
+def nbldpc_code_destroy(handle: int) -> None:
+    lib().nbldpc_code_destroy(handle)
+
+
+def nbldpc_code_info(handle: int):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().nbldpc_code_info(handle, *[ctypes.byref(x) for x in v]), "nbldpc_code_info")
+    return tuple(x.value for x in v)
+
+
+def nbldpc_decode_workspace_size(handle: int, frames: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_decode_workspace_size(handle, int(frames), ctypes.byref(b)),
+           "nbldpc_decode_workspace_size")
+    return b.value
+
+
+def nbldpc_decode_host_workspace_size(handle: int, chunk_frames: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_decode_host_workspace_size(handle, int(chunk_frames), ctypes.byref(b)),
+           "nbldpc_decode_host_workspace_size")
+    return b.value
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def nbldpc_decode(handle: int, gamma, frames: int, max_iters: int, early_stop: int, out_sym, out_iters,
+                  out_ok, workspace, workspace_bytes: int | None = None, stream=None) -> None:
+    """Queue a decode of device buffers on `stream` (default: torch's current stream)."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    st = lib().nbldpc_decode(handle, _ptr(gamma), int(frames), int(max_iters), int(early_stop),
+                             _ptr(out_sym), _ptr(out_iters), _ptr(out_ok), _ptr(workspace),
+                             int(workspace_bytes), _stream_ptr(stream))
+    _check(st, "nbldpc_decode")
+
+
+def nbldpc_decode_host(handle: int, gamma_host, frames: int, max_iters: int, early_stop: int,
+                       out_sym_host, out_iters_host, out_ok_host, chunk_frames: int, workspace,
+                       workspace_bytes: int | None = None, stream=None) -> None:
+    """Queue a decode of host buffers (pinned for overlap); sync `stream` before reading outputs."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    st = lib().nbldpc_decode_host(handle, _ptr(gamma_host), int(frames), int(max_iters), int(early_stop),
+                                  _ptr(out_sym_host), _ptr(out_iters_host), _ptr(out_ok_host),
+                                  int(chunk_frames), _ptr(workspace), int(workspace_bytes),
+                                  _stream_ptr(stream))
+    _check(st, "nbldpc_decode_host")
+
+
+class Decoder:
+    """Owns a code handle; allocates outputs and workspace with torch."""
+
+    def __init__(self, q, prim_poly, n_cols, n_rows, row_ptr, col_idx, coef):
+        self.handle = nbldpc_code_create(q, prim_poly, n_cols, n_rows, row_ptr, col_idx, coef)
+        self.q, self.n, self.m, self.nnz = nbldpc_code_info(self.handle)
+        self._ws = None
+
+    @classmethod
+    def from_code(cls, code):
+        return cls(code.q, code.poly, code.n, code.m, code.row_ptr, code.col_idx, code.coef)
+
+    def close(self):
+        if self.handle:
+            nbldpc_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, frames: int, device) -> torch.Tensor:
+        need = nbldpc_decode_workspace_size(self.handle, frames)
+        if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
+            self._ws = torch.empty(need, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def decode(self, gamma: torch.Tensor, max_iters: int, early_stop: int, stream=None):
+        """(symbols [F, N] uint8, iterations [F] int32, ok [F] uint8) on gamma's device."""
+        assert gamma.is_cuda and gamma.dtype == torch.uint8 and gamma.is_contiguous()
+        f = gamma.shape[0]
+        assert gamma.shape[1:] == (self.n, self.q)
+        dev = gamma.device
+        sym = torch.empty((f, self.n), dtype=torch.uint8, device=dev)
+        its = torch.empty((f,), dtype=torch.int32, device=dev)
+        ok = torch.empty((f,), dtype=torch.uint8, device=dev)
+        ws = self.workspace(f, dev)
+        nbldpc_decode(self.handle, gamma, f, max_iters, early_stop, sym, its, ok, ws, stream=stream)
+        return sym, its, ok
