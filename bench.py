@@ -1,0 +1,319 @@
+"""Throughput benchmark of the GB300 min-max NB-LDPC decoder.
+
+One step decodes the GF(64) (x^6+x+1) regular (2,4) rate-1/2 N=576 workload:
+65536 frames at each of Eb/N0 = 1.5, 2.0 and 2.5 dB (196608 frames, one
+nbldpc_decode call), up to 20 iterations with syndrome early stop.  Inputs
+(7.2 GB of uint8 reliabilities) are synthetic, seeded, and resident in HBM
+before the timed region; they are larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With torchrun, every rank decodes its own
+batch (weak scaling, no data-path collective); the timing is the max over
+ranks.  --impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+WORKLOAD = "gf64_n576_dv2_dc4"
+SM_COUNT = 152
+PEAK_OPS_PER_CLK_SM = 4 * 32 * 2   # packed u16x2 min/max: 4 sub-partitions x 32 lanes x 2 halves
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--frames", type=int, default=None, help="frames per Eb/N0 point (default: 65536)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1 and args.impl == "gb300":
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mma_kernels.cuh", "nbldpc.cu"):
+        with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(per_frame_iter_pairs):
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "mma_decode_kernel_gf64_n576.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_bpf = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_bpf or m_hash.group(1) != kernel_source_hash():
+        return None, path
+    return float(m_bpf.group(1)), path
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs(code, w, frames_per_point, device, rank):
+    from paper_2508_03567_gb300 import inputs as I
+    parts = []
+    for i, eb in enumerate(w["ebn0"]):
+        seed = I.workload_seed(WORKLOAD, i) + 7919 * rank
+        parts.append(I.make_batch(code, eb, seed, frames_per_point, device=device, chunk=8192).gamma)
+    return torch.cat(parts, 0).contiguous()
+
+
+def cpu_oracle_rate(code, w, sample_per_point, threads):
+    """Info Mbit/s of the CPU oracle on a bounded sample of the same workload."""
+    import oracle
+    from paper_2508_03567_gb300 import inputs as I
+    gam = []
+    for i, eb in enumerate(w["ebn0"]):
+        gam.append(I.make_batch(code, eb, I.workload_seed(WORKLOAD, i), sample_per_point).gamma.numpy())
+    g = np.concatenate(gam, 0)
+    t0 = time.perf_counter()
+    oracle.decode(code, g, w["max_iters"], w["early_stop"], threads=threads)
+    dt = time.perf_counter() - t0
+    bits = g.shape[0] * code.k * code.p
+    return bits / dt / 1e6, dt, g.shape[0]
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2508_03567_gb300 import inputs as I
+    w = I.WORKLOADS[WORKLOAD]
+    code = I.workload_code(WORKLOAD)
+    threads = os.cpu_count() or 1
+    sample = 8
+    for _ in range(args.warmup):
+        cpu_oracle_rate(code, w, 2, threads)
+    times, bits = [], 0
+    for _ in range(args.steps):
+        rate, dt, f = cpu_oracle_rate(code, w, sample, threads)
+        times.append(dt)
+        bits += f * code.k * code.p
+    value = bits / sum(times) / 1e6
+    line = {"metric": "decoded info Mbit/s", "value": value, "unit": "Mbit/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "frames_per_step": 3 * sample, "max_iters": w["max_iters"],
+                       "early_stop": True, "ebn0_db": list(w["ebn0"])},
+            "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} frames per Eb/N0 point per step (of 65536)"},
+            "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding, inputs as I
+    w = I.WORKLOADS[WORKLOAD]
+    code = I.workload_code(WORKLOAD)
+    fpp = args.frames or w["frames"]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    gamma = make_inputs(code, w, fpp, dev, rank)
+    frames = gamma.shape[0]
+    dec = binding.Decoder.from_code(code)
+    stream = torch.cuda.Stream(device=dev)
+    sym = torch.empty((frames, code.n), dtype=torch.uint8, device=dev)
+    its = torch.empty((frames,), dtype=torch.int32, device=dev)
+    ok = torch.empty((frames,), dtype=torch.uint8, device=dev)
+    wsb = dec.workspace(frames, dev)
+    mi, es = w["max_iters"], w["early_stop"]
+
+    def step():
+        binding.nbldpc_decode(dec.handle, gamma, frames, mi, es, sym, its, ok, wsb, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = binding.nbldpc_kernel_launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+    launches = binding.nbldpc_kernel_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        torch.distributed.barrier()
+
+    # decode statistics and algorithmic work of one step (identical every step)
+    its_h = its.cpu().numpy().astype(np.int64)
+    ok_h = ok.cpu().numpy()
+    pairs_fi = code.m * 3 * (w["dc"] - 2) * code.q * code.q   # min-max pairs per frame-iteration
+    pairs_step = int(its_h.sum()) * pairs_fi
+    info_bits_step = frames * code.k * code.p
+    value = ws * args.steps * info_bits_step / total_s / 1e6
+    kernel_s = statistics.mean(step_ms) / 1e3
+    achieved_gops = 2 * pairs_step / kernel_s / 1e9           # 16-bit min/max ops per second
+    clocks = clk.summary()
+    peak_gops = SM_COUNT * PEAK_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    bpf, _ = profiled_traffic(pairs_fi)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(binding, dec, code, gamma, mi, es, args, dev)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        rate, dt, f = cpu_oracle_rate(code, w, 64, threads)
+        cpu = {"value": rate, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+               "sample": f"{f} frames (64 per Eb/N0 point) of the same workload, {dt:.1f} s wall"}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "decoded info Mbit/s", "value": value, "unit": "Mbit/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": frames, "q": code.q, "n": code.n,
+                   "k": code.k, "dv": w["dv"], "dc": w["dc"], "ebn0_db": list(w["ebn0"]),
+                   "max_iters": mi, "early_stop": bool(es), "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"frames sharded over {ws} GPU(s)"},
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved_gops / peak_gops,
+                     "traffic": None if bpf is None else bpf * frames,
+                     "peak_kind": "derived: 152 SMs x 256 u16 min/max lanes/clk x 2070 MHz"},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "decode_stats": {"mean_iters": float(its_h.mean()), "fer_proxy_not_ok": float(1 - ok_h.mean()),
+                         "pairs_per_step": pairs_step, "kernel_ms": 1e3 * kernel_s,
+                         "wall_ms_per_step": 1e3 * (t1 - t0) / args.steps},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_e2e(binding, dec, code, gamma_dev, mi, es, args, dev):
+    """Same workload through nbldpc_decode_host: pinned host inputs, copies timed."""
+    frames = gamma_dev.shape[0]
+    g_host = torch.empty(gamma_dev.shape, dtype=torch.uint8, pin_memory=True)
+    g_host.copy_(gamma_dev)
+    sym = torch.empty((frames, code.n), dtype=torch.uint8, pin_memory=True)
+    its = torch.empty((frames,), dtype=torch.int32, pin_memory=True)
+    ok = torch.empty((frames,), dtype=torch.uint8, pin_memory=True)
+    chunk = 16384
+    need = binding.nbldpc_decode_host_workspace_size(dec.handle, chunk)
+    wsb = torch.empty(need, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        binding.nbldpc_decode_host(dec.handle, g_host, frames, mi, es, sym, its, ok, chunk, wsb,
+                                   stream=stream)
+        stream.synchronize()
+
+    for _ in range(2):
+        step()
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    bits = frames * code.k * code.p
+    return {"value": bits / dt / 1e6, "unit": "Mbit/s", "h2d_bytes_per_step": int(g_host.numel()),
+            "d2h_bytes_per_step": int(sym.numel() + 4 * its.numel() + ok.numel()),
+            "ms_per_step": 1e3 * dt, "steps": steps, "chunk_frames": chunk}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

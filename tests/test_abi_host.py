@@ -1,0 +1,83 @@
+"""C-ABI library: loads without a GPU, exports every symbol the header
+declares, and rejects malformed codes on the host before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_03567_gb300 import build, binding
+    build.build_library()
+    return binding
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "nbldpc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nbldpc_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_binding_names(lib):
+    assert header_functions() == sorted(lib.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = lib.lib()
+    for name in header_functions():
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_status_strings(lib):
+    for st in range(0, -8, -1):
+        s = lib.nbldpc_status_string(st)
+        assert s and s != "unknown status"
+    assert lib.nbldpc_status_string(5) == "unknown status"
+
+
+def _create(lib, q, poly, n, m, rp, ci, cf):
+    with pytest.raises(lib.NbldpcError) as ei:
+        lib.nbldpc_code_create(q, poly, n, m, rp, ci, cf)
+    return ei.value.status
+
+
+def test_rejects_bad_field(lib):
+    rp, ci, cf = [0, 2], [0, 1], [1, 1]
+    assert _create(lib, 6, 0x7, 2, 1, rp, ci, cf) == lib.NBLDPC_ERR_POLY      # not a power of two
+    assert _create(lib, 512, 0x211, 2, 1, rp, ci, cf) == lib.NBLDPC_ERR_POLY  # too big
+    assert _create(lib, 16, 0x1F, 2, 1, rp, ci, cf) == lib.NBLDPC_ERR_POLY    # x has order 5
+    assert _create(lib, 4, 0x5, 2, 1, rp, ci, cf) == lib.NBLDPC_ERR_POLY      # reducible
+    assert _create(lib, 8, 0x13, 2, 1, rp, ci, cf) == lib.NBLDPC_ERR_POLY     # wrong degree
+
+
+def test_rejects_bad_matrix(lib):
+    E = lib.NBLDPC_ERR_H
+    assert _create(lib, 4, 0x7, 3, 1, [0, 1], [0], [1]) == E                   # row degree 1
+    assert _create(lib, 4, 0x7, 3, 1, [0, 2], [0, 0], [1, 2]) == E             # column twice in a row
+    assert _create(lib, 4, 0x7, 3, 1, [0, 2], [0, 3], [1, 2]) == E             # column out of range
+    assert _create(lib, 4, 0x7, 3, 1, [0, 2], [0, 1], [1, 4]) == E             # coefficient >= q
+    assert _create(lib, 4, 0x7, 3, 1, [0, 2], [0, 1], [0, 1]) == E             # zero coefficient
+    assert _create(lib, 4, 0x7, 3, 1, [0, 2], [0, 1], [1, 1]) == E             # column 2 unused
+    assert _create(lib, 4, 0x7, 3, 1, [1, 3], [0, 1, 2], [1, 1, 1]) == E       # row_ptr[0] != 0
+
+
+def test_rejects_oversized_code(lib):
+    d = 65
+    assert _create(lib, 4, 0x7, d, 1, [0, d], list(range(d)), [1] * d) == lib.NBLDPC_ERR_UNSUPPORTED
+
+
+def test_rejects_null_arguments(lib):
+    L = lib.lib()
+    h = ctypes.c_void_p()
+    assert L.nbldpc_code_create(4, 7, 2, 1, None, None, None, ctypes.byref(h)) == lib.NBLDPC_ERR_ARG
+    assert L.nbldpc_code_create(4, 7, 2, 1, None, None, None, None) == lib.NBLDPC_ERR_ARG
+    assert L.nbldpc_code_info(None, None, None, None, None) == lib.NBLDPC_ERR_ARG
+    sz = ctypes.c_size_t()
+    assert L.nbldpc_decode_workspace_size(None, 1, ctypes.byref(sz)) == lib.NBLDPC_ERR_ARG
+    assert L.nbldpc_decode(None, None, 1, 1, 1, None, None, None, None, 0, None) == lib.NBLDPC_ERR_ARG

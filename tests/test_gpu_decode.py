@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA decoder (through the C ABI) against the CPU oracle,
+element by element, on seeded inputs; plus edge cases and properties that hold
+at any size.  Bar: bit-exact (every output is an integer decided by integer
+arithmetic with fixed tie-breaks)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2508_03567_gb300 import binding, inputs as I
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu_decode(code, gamma, max_iters, early_stop):
+    dec = binding.Decoder.from_code(code)
+    g = torch.as_tensor(gamma).cuda().contiguous()
+    s, i, o = dec.decode(g, max_iters, early_stop)
+    torch.cuda.synchronize()
+    return s.cpu().numpy(), i.cpu().numpy(), o.cpu().numpy()
+
+
+def assert_same(got, want, ctx=""):
+    names = ("symbols", "iterations", "ok")
+    for n, g, w in zip(names, got, want):
+        if not np.array_equal(g, w):
+            bad = np.nonzero((g != w).reshape(g.shape[0], -1).any(1))[0]
+            raise AssertionError(f"{ctx}: {n} differ in {bad.size} frames, first {bad[:8].tolist()}")
+
+
+# --------------------------------------------------------------- workloads
+SMALL = [("gf4_n48_dv2_dc4", 1000), ("gf64_n576_dv2_dc4", 64), ("gf16_n1024_dv2_dc4", 48),
+         ("gf32_n600_dv3_dc6", 48), ("gf256_n128_dv2_dc8", 16), ("gf256_n384_dv2_dc6", 12)]
+
+
+@pytest.mark.parametrize("name,frames", SMALL)
+def test_workload_parity(name, frames):
+    w = I.WORKLOADS[name]
+    code = I.workload_code(name)
+    for k, eb in enumerate(w["ebn0"]):
+        b = I.make_batch(code, eb, I.workload_seed(name, k) + 1, frames)
+        g = b.gamma.numpy()
+        got = gpu_decode(code, g, w["max_iters"], w["early_stop"])
+        want = oracle.decode(code, g, w["max_iters"], w["early_stop"], threads=THREADS)
+        assert_same(got, want, f"{name} @ {eb} dB")
+
+
+# --------------------------------------------------------------- fields and shapes
+@pytest.mark.parametrize("q,n,dv,dc", [(2, 60, 3, 6), (4, 40, 2, 5), (8, 64, 2, 4), (16, 96, 3, 6),
+                                       (32, 64, 2, 4), (64, 48, 2, 6), (128, 96, 2, 4), (256, 32, 2, 4)])
+def test_every_field_order(q, n, dv, dc):
+    code = I.make_regular_code(q, n, dv, dc, seed=31 * q + n)
+    for eb, early in ((1.0, 1), (2.5, 0)):
+        b = I.make_batch(code, eb, 5 + q, 24)
+        g = b.gamma.numpy()
+        got = gpu_decode(code, g, 9, early)
+        want = oracle.decode(code, g, 9, early, threads=THREADS)
+        assert_same(got, want, f"q={q} early={early}")
+
+
+def irregular_code(q, seed):
+    """Rows of degree 2..9, columns of degree 1..4, random coefficients."""
+    rng = np.random.default_rng(seed)
+    n, m = 70, 30
+    h = np.zeros((m, n), np.int64)
+    for r in range(m):
+        d = int(rng.integers(2, 10))
+        cols = rng.choice(n, d, replace=False)
+        h[r, cols] = rng.integers(1, q, d)
+    for c in range(n):
+        if not h[:, c].any():
+            h[int(rng.integers(m)), c] = int(rng.integers(1, q))
+    return I.code_from_dense(h, q, I.PRIMITIVE_POLY[q])
+
+
+@pytest.mark.parametrize("q", [4, 16, 64, 256])
+def test_irregular_code(q):
+    code = irregular_code(q, q)
+    rng = np.random.default_rng(q + 1)
+    g = rng.integers(0, 40, (20, code.n, q)).astype(np.uint8)
+    hard = rng.integers(0, q, (20, code.n))
+    g[np.arange(20)[:, None], np.arange(code.n)[None, :], hard] = 0
+    for early in (0, 1):
+        got = gpu_decode(code, g, 7, early)
+        want = oracle.decode(code, g, 7, early, threads=THREADS)
+        assert_same(got, want, f"irregular q={q}")
+
+
+# --------------------------------------------------------------- adversarial inputs
+@pytest.mark.parametrize("kind", ["all_equal", "saturated", "random_u8", "zeros", "ties_small", "noiseless"])
+def test_adversarial_inputs(kind):
+    code = I.workload_code("gf64_n576_dv2_dc4")
+    rng = np.random.default_rng(hash(kind) % 1000)
+    f, n, q = 6, code.n, code.q
+    if kind == "all_equal":
+        g = np.full((f, n, q), 9, np.uint8)
+    elif kind == "saturated":
+        g = rng.choice(np.array([0, 255], np.uint8), (f, n, q))
+    elif kind == "random_u8":
+        g = rng.integers(0, 256, (f, n, q)).astype(np.uint8)
+    elif kind == "zeros":
+        g = np.zeros((f, n, q), np.uint8)
+    elif kind == "ties_small":
+        g = rng.integers(0, 2, (f, n, q)).astype(np.uint8)
+    else:
+        g = I.make_batch(code, 2.0, 3, f, noiseless=True).gamma.numpy()
+    for mi, early in ((6, 1), (6, 0), (0, 0), (0, 1), (1, 0)):
+        got = gpu_decode(code, g, mi, early)
+        want = oracle.decode(code, g, mi, early, threads=THREADS)
+        assert_same(got, want, f"{kind} max_iters={mi} early={early}")
+
+
+def test_edge_counts():
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    b = I.make_batch(code, 1.5, 77, 3)
+    g = b.gamma.numpy()
+    # single frame
+    assert_same(gpu_decode(code, g[:1], 30, 1), oracle.decode(code, g[:1], 30, 1), "one frame")
+    # zero frames: nothing queued, no error
+    dec = binding.Decoder.from_code(code)
+    e = torch.empty((0, code.n, code.q), dtype=torch.uint8, device="cuda")
+    s, i, o = dec.decode(e, 5, 1)
+    torch.cuda.synchronize()
+    assert s.shape == (0, code.n)
+
+
+# --------------------------------------------------------------- batch independence, determinism
+def test_frames_independent_of_batch_and_repeatable():
+    code = I.workload_code("gf32_n600_dv3_dc6")
+    b = I.make_batch(code, 2.0, 12, 600)
+    dec = binding.Decoder.from_code(code)
+    g = b.gamma.cuda()
+    full = [t.cpu().numpy() for t in dec.decode(g, 30, 1)]
+    again = [t.cpu().numpy() for t in dec.decode(g, 30, 1)]
+    assert_same(again, full, "repeat")
+    for lo, hi in ((0, 1), (17, 300), (599, 600), (100, 600)):
+        part = [t.cpu().numpy() for t in dec.decode(g[lo:hi].contiguous(), 30, 1)]
+        assert_same(part, [x[lo:hi] for x in full], f"slice {lo}:{hi}")
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    code = I.workload_code("gf64_n576_dv2_dc4")
+    b = I.make_batch(code, 1.5, 21, 700)
+    dec = binding.Decoder.from_code(code)
+    dev = [t.cpu().numpy() for t in dec.decode(b.gamma.cuda(), 20, 1)]
+    gh = b.gamma.pin_memory()
+    f = gh.shape[0]
+    sym = torch.empty((f, code.n), dtype=torch.uint8).pin_memory()
+    its = torch.empty((f,), dtype=torch.int32).pin_memory()
+    ok = torch.empty((f,), dtype=torch.uint8).pin_memory()
+    chunk = 256
+    ws = torch.empty(binding.nbldpc_decode_host_workspace_size(dec.handle, chunk), dtype=torch.uint8,
+                     device="cuda")
+    s = torch.cuda.Stream()
+    binding.nbldpc_decode_host(dec.handle, gh, f, 20, 1, sym, its, ok, chunk, ws, stream=s)
+    s.synchronize()
+    assert_same([sym.numpy(), its.numpy(), ok.numpy()], dev, "host path")
+
+
+def test_workspace_too_small_is_rejected():
+    code = I.workload_code("gf4_n48_dv2_dc4")
+    dec = binding.Decoder.from_code(code)
+    g = torch.zeros((4, code.n, code.q), dtype=torch.uint8, device="cuda")
+    out = torch.empty((4, code.n), dtype=torch.uint8, device="cuda")
+    it = torch.empty(4, dtype=torch.int32, device="cuda")
+    ok = torch.empty(4, dtype=torch.uint8, device="cuda")
+    need = binding.nbldpc_decode_workspace_size(dec.handle, 4)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(binding.NbldpcError) as ei:
+        binding.nbldpc_decode(dec.handle, g, 4, 5, 1, out, it, ok, ws, workspace_bytes=need - 1)
+    assert ei.value.status == binding.NBLDPC_ERR_ARG
+
+
+# --------------------------------------------------------------- full size, as benchmarked
+def test_full_size_gf64_batch_sampled_parity():
+    """The benchmark's launch: 65536 frames at each of 1.5/2.0/2.5 dB in one
+    call; sampled frames against the oracle, every frame against the
+    syndrome property."""
+    name = "gf64_n576_dv2_dc4"
+    w = I.WORKLOADS[name]
+    code = I.workload_code(name)
+    parts = [I.make_batch(code, eb, I.workload_seed(name, k), w["frames"], device="cuda", chunk=8192).gamma
+             for k, eb in enumerate(w["ebn0"])]
+    g = torch.cat(parts, 0).contiguous()
+    del parts
+    dec = binding.Decoder.from_code(code)
+    s, i, o = dec.decode(g, w["max_iters"], w["early_stop"])
+    torch.cuda.synchronize()
+    s, i, o = s.cpu().numpy(), i.cpu().numpy(), o.cpu().numpy()
+    f = g.shape[0]
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([rng.choice(f, 40, replace=False), [0, f - 1, 65535, 65536, 131071]]))
+    gs = g[torch.as_tensor(pick, device="cuda")].cpu().numpy()
+    want = oracle.decode(code, gs, w["max_iters"], w["early_stop"], threads=THREADS)
+    assert_same([s[pick], i[pick], o[pick]], want, "sampled full-size frames")
+    assert i.min() >= 0 and i.max() <= w["max_iters"]
+    okv = oracle.syndrome_ok(code, s)
+    assert np.array_equal(okv, o)
+    assert np.all(i[o == 0] == w["max_iters"])      # early stop: a failed frame ran all iterations
+
+
+def test_full_size_gf256_batch_sampled_parity():
+    name = "gf256_n384_dv2_dc6"
+    w = I.WORKLOADS[name]
+    code = I.workload_code(name)
+    g = I.make_batch(code, w["ebn0"][0], I.workload_seed(name, 0), w["frames"], device="cuda",
+                     chunk=2048).gamma
+    dec = binding.Decoder.from_code(code)
+    s, i, o = dec.decode(g, w["max_iters"], w["early_stop"])
+    torch.cuda.synchronize()
+    s, i, o = s.cpu().numpy(), i.cpu().numpy(), o.cpu().numpy()
+    pick = np.array([0, 1, 4097, 9000, 16383])
+    want = oracle.decode(code, g[torch.as_tensor(pick, device="cuda")].cpu().numpy(), w["max_iters"],
+                         w["early_stop"], threads=THREADS)
+    assert_same([s[pick], i[pick], o[pick]], want, "sampled GF(256) frames")
+    assert np.array_equal(oracle.syndrome_ok(code, s), o)
+
+
+def test_generator_is_device_independent():
+    code = I.workload_code("gf64_n576_dv2_dc4")
+    a = I.make_batch(code, 2.0, 99, 40, device="cpu")
+    b = I.make_batch(code, 2.0, 99, 40, device="cuda")
+    assert torch.equal(a.gamma, b.gamma.cpu()) and torch.equal(a.codewords, b.codewords.cpu())
