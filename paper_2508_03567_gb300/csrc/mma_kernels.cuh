@@ -7,19 +7,12 @@
 // Message vectors (q reliabilities in 0..255) travel between the passes as q
 // bytes per Tanner-graph edge in a per-block global slot that stays resident
 // in L1/L2.  Inside the check-node pass a vector lives in shared memory as q
-// 16-bit lanes packed two per 32-bit word ("pair layout", below), so that the
-// min-max convolution runs on packed max.u16x2 / min.u16x2 instructions.
+// 16-bit values, so that the min-max convolution (see mm_conv) runs on packed
+// max.u16x2 / min.u16x2 instructions, two symbols per instruction.
 //
 // Min-max convolution (Alg. 2, F/B/beta equations, with the coefficient
 // permutation applied to the inputs):
 //     C(x) = min over y of max(A(y), B(x ^ y)),   x, y in GF(2^p).
-// A group of G lanes computes one convolution.  With x = xh*DN + l and
-// y = yh*DN + (l ^ d), the lane-offset d runs over DN = 2^LB values and each
-// lane keeps XN = 2^XB outputs in registers; A values reach lane l from lane
-// l^d through shfl.xor, and the B values a lane needs for offset d are
-// B(j*DN + d), j = xh ^ yh, held in registers, so no dynamic register
-// indexing is needed.  SB high lane bits split the y range further; their
-// partial minima are combined by a shuffle reduce-scatter at the end.
 #pragma once
 
 #include <cstdint>
@@ -40,10 +33,13 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
 }
 __device__ __forceinline__ uint32_t swap16(uint32_t a) { return __byte_perm(a, 0, 0x1032); }
 
+
 // ---------------------------------------------------------------- geometry
-// LB: lane bits of the shuffle offset d; SB: lane bits splitting y.
+// LB: lane bits of x (the shuffle offset d runs over them); SB: lane bits that
+// split the register part of y between lanes.  XB = p - LB register bits of x
+// per lane, TB = XB - SB register bits of y per lane.
 template <int Q> struct Layout;
-template <> struct Layout<2>   { static constexpr int LB = 0, SB = 0; };
+template <> struct Layout<2>   { static constexpr int LB = 1, SB = 0; };
 template <> struct Layout<4>   { static constexpr int LB = 1, SB = 0; };
 template <> struct Layout<8>   { static constexpr int LB = 1, SB = 1; };
 template <> struct Layout<16>  { static constexpr int LB = 2, SB = 1; };
@@ -59,99 +55,97 @@ template <int Q> struct Geo {
   static constexpr int LB = Layout<Q>::LB, SB = Layout<Q>::SB;
   static constexpr int XB = P - LB;             // register bits of x
   static constexpr int TB = XB - SB;            // register bits of y
-  static constexpr int G = 1 << (LB + SB);      // lanes per group
-  static constexpr int DN = 1 << LB;            // shuffle offsets
+  static constexpr int G = 1 << (LB + SB);      // lanes per convolution group
+  static constexpr int DN = 1 << LB;            // x values per register slot (lane part)
+  static constexpr int DS = DN / 2;             // shuffle steps (even offsets d = 2*ds)
   static constexpr int XN = 1 << XB;            // accumulators per lane
-  static constexpr int AW = 1 << (TB - 1);      // packed A words per lane
-  static constexpr int KW = XN / 2;             // packed B words per offset
-  static constexpr int DC = (DN * KW <= 32) ? DN : 32 / KW;  // offsets per B chunk
-  static constexpr int W = Q / 2;               // packed words per vector
-  static constexpr int BPL = Q / G;             // bytes per lane in byte-wise passes
-  static constexpr int VB = (2 * Q + 15) / 16 * 16;  // bytes per packed vector in smem
-  static_assert(TB >= 1 && XB == SB + TB, "layout");
-  static_assert(AW * G == W, "own words cover the vector");
-  static_assert(BPL == 2 || BPL == 4 || BPL == 8, "byte lanes");
+  static constexpr int AWN = 1 << TB;           // packed A words per lane
+  static constexpr int DC = (DS * XN <= 32) ? DS : 32 / XN;   // steps per B chunk (<= 32 regs)
+  static constexpr int OPL = 1 << TB;           // outputs per lane
+  static constexpr int W = Q / 2;               // 32-bit words per vector
+  static constexpr int BPL = Q / G;             // bytes per lane when a group writes q bytes
+  static constexpr int VB = (2 * Q + 15) / 16 * 16;  // bytes per 16-bit vector in smem
+  // variable-node pass: VG lanes per variable node, VBPL bytes each
+  static constexpr int VBPL = Q >= 256 ? 8 : (Q >= 4 ? 4 : 2);
+  static constexpr int VG = Q / VBPL;
+  static_assert(LB >= 1 && TB >= 0 && XB == SB + TB, "layout");
+  static_assert(G <= 32 && G * OPL == Q, "group covers the field");
+  static_assert(DS % DC == 0, "chunking");
 };
 
-// Pair layout: word w = kk*DN + vl holds v0 = 2*kk*DN + vl (low 16 bits) and
-// v0 + DN (high 16 bits).  Index of value v as a 16-bit element:
-template <int Q> __device__ __forceinline__ int pair_index(int v) {
-  using g = Geo<Q>;
-  const int word = ((v >> (g::LB + 1)) << g::LB) | (v & (g::DN - 1));
-  return 2 * word + ((v >> g::LB) & 1);
-}
-
 // ---------------------------------------------------------------- convolution
-// C = A (*) B in pair layout; s, l: lane coordinates inside the group.
-// Inputs and output must not alias.  Caller syncs the group afterwards.
+// C = A (*) B: C(x) = min_y max(A(y), B(x ^ y)); vectors are q 16-bit values
+// in natural order (element v at 16-bit index v).  A group of G lanes; lane
+// (s, l) owns x = xh * DN + l for the XN values of xh and the y values with
+// register part yr in [s * 2^TB, (s + 1) * 2^TB).  A packed A word pairs the
+// lane positions (l, l ^ 1), so offset d = 2*ds reaches lane positions l ^ d
+// and l ^ d ^ 1 in one shuffle, and the matching B values B(j*DN + d),
+// B(j*DN + d + 1) form one natural 32-bit word whatever the parity of x.
+// Accumulator slot r holds xh = r ^ (s << TB), which makes the B register
+// index r ^ t independent of the lane and lets the final reduce-scatter keep
+// and send fixed slots.  Inputs and output must not alias; the caller syncs
+// the group afterwards.
 template <int Q>
 __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
-                                        uint32_t* __restrict__ C, int s, int l, unsigned gmask) {
+                                        uint16_t* __restrict__ C, int s, int l, unsigned gmask) {
   using g = Geo<Q>;
-  uint32_t aown[g::AW];
+  uint32_t aown[g::AWN];
 #pragma unroll
-  for (int u = 0; u < g::AW; ++u) aown[u] = A[(s * g::AW + u) * g::DN + l];
+  for (int t = 0; t < g::AWN; ++t) {
+    const uint32_t w = A[(((s << g::TB) | t) * g::DN + (l & ~1)) >> 1];
+    aown[t] = (l & 1) ? swap16(w) : w;
+  }
   uint32_t acc[g::XN];
 #pragma unroll
   for (int x = 0; x < g::XN; ++x) acc[x] = 0xFFFFFFFFu;
 
 #pragma unroll
-  for (int c0 = 0; c0 < g::DN; c0 += g::DC) {
-    uint32_t bl[g::DC][g::KW];
+  for (int c0 = 0; c0 < g::DS; c0 += g::DC) {
+    uint32_t bl[g::DC][g::XN];
 #pragma unroll
-    for (int k = 0; k < g::KW; ++k) {
-      const uint32_t* row = B + (k ^ (s * g::AW)) * g::DN + c0;
+    for (int j = 0; j < g::XN; ++j) {
+      const uint32_t* row = B + j * g::DS + c0;
       if constexpr (g::DC % 4 == 0) {
 #pragma unroll
         for (int dd = 0; dd < g::DC; dd += 4) {
           const uint4 v = *reinterpret_cast<const uint4*>(row + dd);
-          bl[dd][k] = v.x; bl[dd + 1][k] = v.y; bl[dd + 2][k] = v.z; bl[dd + 3][k] = v.w;
+          bl[dd][j] = v.x; bl[dd + 1][j] = v.y; bl[dd + 2][j] = v.z; bl[dd + 3][j] = v.w;
         }
       } else if constexpr (g::DC % 2 == 0) {
 #pragma unroll
         for (int dd = 0; dd < g::DC; dd += 2) {
           const uint2 v = *reinterpret_cast<const uint2*>(row + dd);
-          bl[dd][k] = v.x; bl[dd + 1][k] = v.y;
+          bl[dd][j] = v.x; bl[dd + 1][j] = v.y;
         }
       } else {
 #pragma unroll
-        for (int dd = 0; dd < g::DC; ++dd) bl[dd][k] = row[dd];
+        for (int dd = 0; dd < g::DC; ++dd) bl[dd][j] = row[dd];
       }
     }
 #pragma unroll
     for (int dd = 0; dd < g::DC; ++dd) {
-      const int d = c0 + dd;
-      uint32_t a[g::AW], as[g::AW];
+      const int d = 2 * (c0 + dd);
+      uint32_t a[g::AWN];
 #pragma unroll
-      for (int u = 0; u < g::AW; ++u) {
-        a[u] = (d == 0) ? aown[u] : __shfl_xor_sync(gmask, aown[u], d);
-        as[u] = swap16(a[u]);
-      }
+      for (int t = 0; t < g::AWN; ++t) a[t] = (d == 0) ? aown[t] : __shfl_xor_sync(gmask, aown[t], d);
 #pragma unroll
-      for (int xh = 0; xh < g::XN; ++xh)
+      for (int r = 0; r < g::XN; ++r)
 #pragma unroll
-        for (int u = 0; u < g::AW; ++u)
-          acc[xh] = vmin2(acc[xh], vmax2((xh & 1) ? as[u] : a[u], bl[dd][(xh >> 1) ^ u]));
+        for (int t = 0; t < g::AWN; ++t) acc[r] = vmin2(acc[r], vmax2(a[t], bl[dd][r ^ t]));
     }
   }
-  // Reduce-scatter over the SB lane bits: afterwards slot r holds x-block
-  // xh = s * 2^TB + r.
+  // reduce-scatter over the SB lane bits: keep slot r, receive the partner's r | 2^c
 #pragma unroll
   for (int b = g::SB - 1; b >= 0; --b) {
     const int c = g::TB + b;
-    const bool sb = (s >> b) & 1;
 #pragma unroll
-    for (int x0 = 0; x0 < (1 << c); ++x0) {
-      const uint32_t send = sb ? acc[x0] : acc[x0 + (1 << c)];
-      const uint32_t keep = sb ? acc[x0 + (1 << c)] : acc[x0];
-      const uint32_t recv = __shfl_xor_sync(gmask, send, 1 << (g::LB + b));
-      acc[x0] = vmin2(keep, recv);
-    }
+    for (int r = 0; r < (1 << c); ++r)
+      acc[r] = vmin2(acc[r], __shfl_xor_sync(gmask, acc[r | (1 << c)], 1 << (g::LB + b)));
   }
 #pragma unroll
-  for (int r = 0; r < g::AW; ++r) {
-    const uint32_t e = acc[2 * r], o = acc[2 * r + 1];
-    C[(s * g::AW + r) * g::DN + l] = vmin2(__byte_perm(e, o, 0x5410), __byte_perm(e, o, 0x7632));
+  for (int r = 0; r < g::OPL; ++r) {
+    const uint32_t v = vmin2(acc[r], acc[r] >> 16);
+    C[(((s << g::TB) | r) * g::DN) + l] = (uint16_t)v;
   }
 }
 
@@ -179,11 +173,13 @@ template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax)
   return ((dmax * Q + 15) / 16) * 16 + (2 * dmax + 3) * Geo<Q>::VB;
 }
 
-template <int BPL> __device__ __forceinline__ void load_bytes(const uint8_t* p, int (&v)[BPL]) {
-  if constexpr (BPL == 2) {
+template <int N> __device__ __forceinline__ void load_bytes(const uint8_t* p, int (&v)[N]) {
+  if constexpr (N == 1) {
+    v[0] = *p;
+  } else if constexpr (N == 2) {
     const uint32_t w = *reinterpret_cast<const uint16_t*>(p);
     v[0] = w & 0xFF; v[1] = w >> 8;
-  } else if constexpr (BPL == 4) {
+  } else if constexpr (N == 4) {
     const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = (w >> (8 * i)) & 0xFF;
@@ -194,10 +190,12 @@ template <int BPL> __device__ __forceinline__ void load_bytes(const uint8_t* p, 
   }
 }
 
-template <int BPL> __device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[BPL]) {
-  if constexpr (BPL == 2) {
+template <int N> __device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[N]) {
+  if constexpr (N == 1) {
+    *p = (uint8_t)v[0];
+  } else if constexpr (N == 2) {
     *reinterpret_cast<uint16_t*>(p) = (uint16_t)(v[0] | (v[1] << 8));
-  } else if constexpr (BPL == 4) {
+  } else if constexpr (N == 4) {
     *reinterpret_cast<uint32_t*>(p) = (uint32_t)(v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24));
   } else {
     uint2 w;
@@ -217,10 +215,15 @@ template <int G> __device__ __forceinline__ void group_sync(unsigned gmask) {
   if constexpr (G > 1) __syncwarp(gmask);
 }
 
+template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
+  return (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
 // ---------------------------------------------------------------- the kernel
 template <int Q>
-__global__ void __launch_bounds__(256) mma_decode_kernel(const DecodeParams p) {
+__global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p) {
   using g = Geo<Q>;
+  constexpr int PW = (g::W + g::G - 1) / g::G;   // permutation words per lane
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sblob = smem;
   uint8_t* chat = smem + p.off.bytes;                                    // [n]
@@ -241,16 +244,43 @@ __global__ void __launch_bounds__(256) mma_decode_kernel(const DecodeParams p) {
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  // check-node groups (G lanes per check)
   const int grp = tid / g::G, ngroups = blockDim.x / g::G;
   const int gl = tid % g::G;
-  const unsigned gmask = (g::G == 32) ? 0xFFFFFFFFu : (((1u << g::G) - 1u) << (lane & ~(g::G - 1)));
+  const unsigned gmask = group_mask<g::G>(lane);
   const int s = gl >> g::LB, l = gl & (g::DN - 1);
+  // variable-node groups (VG lanes per variable node)
+  const int vgrp = tid / g::VG, nvgroups = blockDim.x / g::VG;
+  const int vgl = tid % g::VG;
+  const unsigned vmask = group_mask<g::VG>(lane);
+
+  // lane constants for the coefficient permutations: logarithms of the
+  // symbols this lane gathers (permutation) and writes (de-permutation); the
+  // zero symbol, which every multiplication fixes, is flagged separately.
+  // Packed 8 bits per symbol (q <= 256 keeps every logarithm below 255).
+  uint32_t py_log0 = 0, py_log1 = 0, py_nz0 = 0;   // word i: bits [8i, 8i+8)
+#pragma unroll
+  for (int i = 0; i < PW; ++i) {
+    const int w = gl + i * g::G;
+    if (w < g::W) {
+      if (w) { py_log0 |= (uint32_t)glog[2 * w] << (8 * i); py_nz0 |= 1u << i; }
+      py_log1 |= (uint32_t)glog[2 * w + 1] << (8 * i);
+    }
+  }
+  uint64_t da_log = 0;
+  uint32_t da_mask = 0;
+#pragma unroll
+  for (int i = 0; i < g::BPL; ++i) {
+    const int a = gl * g::BPL + i;
+    if (a) { da_log |= (uint64_t)glog[a] << (8 * i); da_mask |= 1u << i; }
+  }
 
   unsigned char* gs = scratch_base + (size_t)grp * p.group_bytes;
   uint8_t* stage = gs;                                                   // [dmax][q] bytes
   unsigned char* vecs = gs + ((p.dmax * Q + 15) / 16) * 16;
   auto vec = [&](int i) { return reinterpret_cast<uint32_t*>(vecs + (size_t)i * g::VB); };
-  // vectors: P_j = vec(j), F_j = vec(dmax + j), Bv[2] = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
+  auto vec16 = [&](int i) { return reinterpret_cast<uint16_t*>(vecs + (size_t)i * g::VB); };
+  // vectors: P_j = vec(j), F_j = vec(dmax + j), B ping-pong = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
   uint8_t* X = p.msg + (size_t)blockIdx.x * p.slot_bytes;
 
   const int qm1 = Q - 1;
@@ -262,37 +292,39 @@ __global__ void __launch_bounds__(256) mma_decode_kernel(const DecodeParams p) {
     if (frame >= p.frames) break;
     const uint8_t* gam = p.gamma + (size_t)frame * p.n * Q;
 
-    // ---- variable-node pass: S = gamma + sum beta, decision, alpha = sat(S - beta - min)
+    // ---- variable-node pass (Alg. 2, VNP and hard decision):
+    //   S(a) = gamma(a) + sum over edges of beta(a);  c = argmin S (lowest a)
+    //   alpha_e(a) = min(255, (S - beta_e)(a) - min_b (S - beta_e)(b))
     auto vnp = [&](bool first, bool want_alpha) {
-      for (int vn = grp; vn < p.n; vn += ngroups) {
-        int S[g::BPL];
-        load_bytes<g::BPL>(gam + (size_t)vn * Q + gl * g::BPL, S);
+      for (int vn = vgrp; vn < p.n; vn += nvgroups) {
+        int S[g::VBPL];
+        load_bytes<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
         const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
         if (!first) {
           for (int k = k0; k < k1; ++k) {
-            int b[g::BPL];
-            load_bytes<g::BPL>(X + (size_t)vn_edge[k] * Q + gl * g::BPL, b);
+            int b[g::VBPL];
+            load_bytes<g::VBPL>(X + (size_t)vn_edge[k] * Q + vgl * g::VBPL, b);
 #pragma unroll
-            for (int i = 0; i < g::BPL; ++i) S[i] += b[i];
+            for (int i = 0; i < g::VBPL; ++i) S[i] += b[i];
           }
         }
         int key = 0x7FFFFFFF;
 #pragma unroll
-        for (int i = 0; i < g::BPL; ++i) key = min(key, (S[i] << 8) | (gl * g::BPL + i));
-        key = group_min<g::G>(key, gmask);
-        if (gl == 0) chat[vn] = (uint8_t)(key & 0xFF);
+        for (int i = 0; i < g::VBPL; ++i) key = min(key, (S[i] << 8) | (vgl * g::VBPL + i));
+        key = group_min<g::VG>(key, vmask);
+        if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
         if (!first && want_alpha) {
           for (int k = k0; k < k1; ++k) {
-            uint8_t* row = X + (size_t)vn_edge[k] * Q + gl * g::BPL;
-            int t[g::BPL];
-            load_bytes<g::BPL>(row, t);
+            uint8_t* row = X + (size_t)vn_edge[k] * Q + vgl * g::VBPL;
+            int t[g::VBPL];
+            load_bytes<g::VBPL>(row, t);
             int mn = 0x7FFFFFFF;
 #pragma unroll
-            for (int i = 0; i < g::BPL; ++i) { t[i] = S[i] - t[i]; mn = min(mn, t[i]); }
-            mn = group_min<g::G>(mn, gmask);
+            for (int i = 0; i < g::VBPL; ++i) { t[i] = S[i] - t[i]; mn = min(mn, t[i]); }
+            mn = group_min<g::VG>(mn, vmask);
 #pragma unroll
-            for (int i = 0; i < g::BPL; ++i) t[i] = min(255, t[i] - mn);
-            store_bytes<g::BPL>(row, t);
+            for (int i = 0; i < g::VBPL; ++i) t[i] = min(255, t[i] - mn);
+            store_bytes<g::VBPL>(row, t);
           }
         }
       }
@@ -312,7 +344,7 @@ __global__ void __launch_bounds__(256) mma_decode_kernel(const DecodeParams p) {
       return __syncthreads_or(bad) == 0;
     };
 
-    // ---- check-node pass (F, B, beta) for every check, one group per check
+    // ---- check-node pass (Alg. 2, F & B matrices and beta), one group per check
     auto cnp = [&](bool first) {
       for (int r = grp; r < p.m; r += ngroups) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
@@ -332,59 +364,54 @@ __global__ void __launch_bounds__(256) mma_decode_kernel(const DecodeParams p) {
           }
         }
         group_sync<g::G>(gmask);
-        // permutation: P_j(y) = alpha_j(h_j^-1 y), stored in pair layout
+        // permutation: P_j(y) = alpha_j(h_j^-1 y), 16-bit natural order
         for (int j = 0; j < d; ++j) {
           const int lhinv = (qm1 - edge_lh[e0 + j]) % qm1;
           const uint8_t* a = stage + j * Q;
           uint32_t* P = vec(j);
 #pragma unroll
-          for (int u = 0; u < g::AW; ++u) {
-            const int w = gl + u * g::G;
-            const int kk = w >> g::LB, vl = w & (g::DN - 1);
-            const int v0 = (kk << (g::LB + 1)) | vl, v1 = v0 | g::DN;
-            const int s0 = v0 ? exp2[glog[v0] + lhinv] : 0;
-            const int s1 = exp2[glog[v1] + lhinv];
-            P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
+          for (int i = 0; i < PW; ++i) {
+            const int w = gl + i * g::G;
+            if (PW * g::G == g::W || w < g::W) {
+              const int s0 = (py_nz0 >> i) & 1 ? exp2[((py_log0 >> (8 * i)) & 0xFF) + lhinv] : 0;
+              const int s1 = exp2[((py_log1 >> (8 * i)) & 0xFF) + lhinv];
+              P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
+            }
           }
         }
         group_sync<g::G>(gmask);
         // beta_j(a) = R_j(h_j a), written over the edge's message row
-        auto depermute = [&](const uint32_t* Rv, int e) {
-          const uint16_t* R16 = reinterpret_cast<const uint16_t*>(Rv);
+        auto depermute = [=](const uint16_t* R16, int e) {
           const int lh = edge_lh[e];
           int out[g::BPL];
 #pragma unroll
-          for (int i = 0; i < g::BPL; ++i) {
-            const int a = gl * g::BPL + i;
-            const int v = a ? exp2[glog[a] + lh] : 0;
-            out[i] = R16[pair_index<Q>(v)];
-          }
+          for (int i = 0; i < g::BPL; ++i) out[i] = R16[(da_mask >> i) & 1 ? exp2[((da_log >> (8 * i)) & 0xFF) + lh] : 0];
           store_bytes<g::BPL>(X + (size_t)e * Q + gl * g::BPL, out);
         };
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
-        const uint32_t* Fprev = vec(0);
+        int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<Q>(Fprev, vec(j), vec(p.dmax + j), s, l, gmask);
+          mm_conv<Q>(vec(fprev), vec(j), vec16(p.dmax + j), s, l, gmask);
           group_sync<g::G>(gmask);
-          Fprev = vec(p.dmax + j);
+          fprev = p.dmax + j;
         }
-        depermute(Fprev, e0 + d - 1);                      // beta_{d-1} from F_{d-2}
+        depermute(vec16(fprev), e0 + d - 1);               // beta_{d-1} from F_{d-2}
         // backward: B_{d-1} = P_{d-1}; beta_j from F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j
-        const uint32_t* Bcur = vec(d - 1);
+        int bcur = d - 1;
         int pp = 0;
         for (int j = d - 2; j >= 1; --j) {
-          const uint32_t* Fj = (j == 1) ? vec(0) : vec(p.dmax + j - 1);
-          uint32_t* R = vec(2 * p.dmax + 2);
-          mm_conv<Q>(Fj, Bcur, R, s, l, gmask);
+          const int fj = (j == 1) ? 0 : p.dmax + j - 1;
+          const int rv = 2 * p.dmax + 2;
+          mm_conv<Q>(vec(fj), vec(bcur), vec16(rv), s, l, gmask);
           group_sync<g::G>(gmask);
-          depermute(R, e0 + j);
-          uint32_t* Bn = vec(2 * p.dmax + pp);
-          mm_conv<Q>(Bcur, vec(j), Bn, s, l, gmask);
+          depermute(vec16(rv), e0 + j);
+          const int bn = 2 * p.dmax + pp;
+          mm_conv<Q>(vec(bcur), vec(j), vec16(bn), s, l, gmask);
           group_sync<g::G>(gmask);
-          Bcur = Bn;
+          bcur = bn;
           pp ^= 1;
         }
-        depermute(Bcur, e0);                               // beta_0 from B_1
+        depermute(vec16(bcur), e0);                        // beta_0 from B_1
         group_sync<g::G>(gmask);
       }
     };
