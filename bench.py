@@ -33,7 +33,7 @@ import torch  # noqa: E402
 
 WORKLOAD = "gf64_n576_dv2_dc4"
 SM_COUNT = 152
-PEAK_OPS_PER_CLK_SM = 4 * 32 * 2   # packed u16x2 min/max: 4 sub-partitions x 32 lanes x 2 halves
+PEAK_OPS_PER_CLK_SM = 4 * 16 * 2   # ALU pipe: 4 sub-partitions x 16 lanes/clk x 2 halves of u16x2 min/max
 SM_MAX_MHZ = 2070.0
 
 
@@ -270,7 +270,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops,
                      "traffic": None if bpf is None else bpf * frames,
-                     "peak_kind": "derived: 152 SMs x 256 u16 min/max lanes/clk x 2070 MHz"},
+                     "peak_kind": "derived (of fallback clocks): 152 SMs x 128 u16 min/max ops/clk (ALU pipe) x 2070 MHz"},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,
