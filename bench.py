@@ -34,7 +34,16 @@ import torch  # noqa: E402
 WORKLOAD = "gf64_n576_dv2_dc4"
 SM_COUNT = 152
 PEAK_OPS_PER_CLK_SM = 4 * 16 * 2   # ALU pipe: 4 sub-partitions x 16 lanes/clk x 2 halves of u16x2 min/max
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def sm_max_mhz():
+    """Maximum SM clock: the measured-peaks file written for this GPU pool, else 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return SM_MAX_MHZ_FALLBACK, "fallback"
 
 
 def parse():
@@ -243,7 +252,8 @@ def main():
     kernel_s = statistics.mean(step_ms) / 1e3
     achieved_gops = 2 * pairs_step / kernel_s / 1e9           # 16-bit min/max ops per second
     clocks = clk.summary()
-    peak_gops = SM_COUNT * PEAK_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    mhz, mhz_kind = sm_max_mhz()
+    peak_gops = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
     bpf, _ = profiled_traffic(pairs_fi)
 
     e2e = None
@@ -270,7 +280,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops,
                      "traffic": None if bpf is None else bpf * frames,
-                     "peak_kind": "derived (of fallback clocks): 152 SMs x 128 u16 min/max ops/clk (ALU pipe) x 2070 MHz"},
+                     "peak_kind": f"derived: 152 SMs x 128 u16 min/max ops/clk (ALU pipe) x {mhz:.0f} MHz ({mhz_kind} max SM clock)"},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,
