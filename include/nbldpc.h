@@ -138,6 +138,43 @@ int nbldpc_decode_host(const nbldpc_code *code, const uint8_t *gamma_host, int f
                        size_t workspace_bytes, void *cuda_stream);
 
 /*
+ * Size of the fixed device array that nbldpc_decode_noalloc works in.
+ */
+#define NBLDPC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * nbldpc_decode without a workspace argument and without any allocation.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc or hand over device scratch: for example a receiver
+ * or plugin that must not allocate device memory once it is running, or code
+ * that runs inside a framework whose allocator owns all device memory and
+ * exposes no way to borrow scratch from it.
+ *
+ * Same arguments, semantics and results as nbldpc_decode, minus the
+ * workspace.  The scratch is one file-scope device array of
+ * NBLDPC_NOALLOC_SCRATCH_BYTES (32 MiB), created with the library's module on
+ * every GPU that loads it and held until the process exits.  The array holds
+ * the frame counter (cleared by each call, stream-ordered) and one message
+ * slot of nnz*q bytes per resident block; when fewer slots fit than the
+ * device can keep resident, the call launches fewer blocks (same results,
+ * lower throughput).  A code whose slot alone exceeds the array is rejected
+ * with NBLDPC_ERR_UNSUPPORTED before anything is queued.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Nothing is allocated by this function: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ * All calls share the one array, and each call leaves its own contents
+ * there.  Calls whose work overlaps on the GPU (different streams, different
+ * threads, or different handles) race on it and give undefined results;
+ * serialize them, for instance by queueing them on one stream.
+ */
+int nbldpc_decode_noalloc(const nbldpc_code *code, const uint8_t *gamma_dev, int frames, int max_iters,
+                          int early_stop, uint8_t *out_sym_dev, int32_t *out_iters_dev,
+                          uint8_t *out_ok_dev, void *cuda_stream);
+
+/*
  * Number of decode-kernel launches the calls above queued since the library
  * was loaded (all threads, all handles).  Launch accounting for benchmarks.
  */

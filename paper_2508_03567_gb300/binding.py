@@ -28,7 +28,8 @@ NBLDPC_ERR_UNSUPPORTED = -7
 
 EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_workspace_size", "nbldpc_decode", "nbldpc_decode_host_workspace_size",
-            "nbldpc_decode_host", "nbldpc_kernel_launch_count", "nbldpc_status_string")
+            "nbldpc_decode_host", "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
+            "nbldpc_status_string")
 
 _lib = None
 _lock = threading.Lock()
@@ -63,6 +64,8 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_decode_host_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_decode_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                              vp, ctypes.c_int, vp, sz, vp]
+            L.nbldpc_decode_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                                vp, vp]
             L.nbldpc_kernel_launch_count.argtypes = []
             L.nbldpc_kernel_launch_count.restype = ctypes.c_uint64
             L.nbldpc_status_string.argtypes = [ctypes.c_int]
@@ -162,6 +165,16 @@ def nbldpc_decode_host(handle: int, gamma_host, frames: int, max_iters: int, ear
                                   int(chunk_frames), _ptr(workspace), int(workspace_bytes),
                                   _stream_ptr(stream))
     _check(st, "nbldpc_decode_host")
+
+
+def nbldpc_decode_noalloc(handle: int, gamma, frames: int, max_iters: int, early_stop: int, out_sym,
+                          out_iters, out_ok, stream=None) -> None:
+    """Queue a decode that uses the library's fixed device scratch instead of a
+    caller workspace (for callers that cannot allocate device memory).  Calls
+    that overlap on the GPU share that scratch and race; queue them in order."""
+    st = lib().nbldpc_decode_noalloc(handle, _ptr(gamma), int(frames), int(max_iters), int(early_stop),
+                                     _ptr(out_sym), _ptr(out_iters), _ptr(out_ok), _stream_ptr(stream))
+    _check(st, "nbldpc_decode_noalloc")
 
 
 class Decoder:

@@ -184,9 +184,82 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// ---- non-allocating decode (nbldpc_decode_noalloc) -------------------------
+// Fixed scratch for callers that cannot allocate: frame counter + message slots.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NBLDPC_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per
+// device, with that device current; host code must not use the symbol itself).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NBLDPC_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NBLDPC_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return NBLDPC_OK;
+}
+
+int launch_noalloc(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
+                   uint8_t* sym, int32_t* iters, uint8_t* ok, void* scratch, int grid, cudaStream_t st) {
+  nbldpc::DecodeParams prm{};
+  prm.gamma = gamma;
+  prm.out_sym = sym;
+  prm.out_iters = iters;
+  prm.out_ok = ok;
+  prm.counter = reinterpret_cast<unsigned int*>(scratch);
+  prm.msg = reinterpret_cast<uint8_t*>(scratch) + 256;
+  prm.blob = c->blob_dev;
+  prm.off = c->off;
+  prm.slot_bytes = slot_bytes(c);
+  prm.n = c->n;
+  prm.m = c->m;
+  prm.nnz = c->nnz;
+  prm.dmax = c->dmax;
+  prm.frames = frames;
+  prm.max_iters = max_iters;
+  prm.early_stop = early_stop ? 1 : 0;
+  prm.group_bytes = c->cfg.group_bytes;
+  // the array keeps the previous call's contents: the frame counter must start at zero
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  void* args[] = {&prm};
+  e = cudaLaunchKernel(kernel_for(c->q), dim3(grid), dim3(c->cfg.threads), args, (size_t)c->cfg.smem, st);
+  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return NBLDPC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int frames, int max_iters,
+                          int early_stop, uint8_t* out_sym_dev, int32_t* out_iters_dev, uint8_t* out_ok_dev,
+                          void* cuda_stream) {
+  if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
+  if (frames == 0) return NBLDPC_OK;
+  if (!gamma_dev || !out_sym_dev || !out_iters_dev || !out_ok_dev) return NBLDPC_ERR_ARG;
+  if (!aligned(gamma_dev, 16) || !aligned(out_iters_dev, 4)) return NBLDPC_ERR_ARG;
+  const size_t slot = slot_bytes(c);
+  if (256 + slot > (size_t)NBLDPC_NOALLOC_SCRATCH_BYTES) return NBLDPC_ERR_UNSUPPORTED;
+  const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / slot);
+  int grid = grid_for(c, frames);
+  if (grid > fit) grid = fit;
+  int st = cuda_status(cudaGetLastError());
+  if (st != NBLDPC_OK) return st;
+  void* scratch = nullptr;
+  st = noalloc_scratch(&scratch);
+  if (st != NBLDPC_OK) return st;
+  return launch_noalloc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev,
+                        scratch, grid, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
 
 const char* nbldpc_status_string(int status) {
   switch (status) {
