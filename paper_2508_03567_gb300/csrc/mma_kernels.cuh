@@ -8,7 +8,8 @@
 // bytes per Tanner-graph edge in a per-block global slot that stays resident
 // in L1/L2.  Inside the check-node pass a vector lives in shared memory as q
 // 16-bit values, so that the min-max convolution (see mm_conv) runs on packed
-// max.u16x2 / min.u16x2 instructions, two symbols per instruction.
+// max.u16x2 / min.u16x2 instructions, two symbols per instruction; the
+// variable-node pass also works on 16-bit pairs held in 32-bit registers.
 //
 // Min-max convolution (Alg. 2, F/B/beta equations, with the coefficient
 // permutation applied to the inputs):
@@ -31,8 +32,19 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
   asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
   return d;
 }
-__device__ __forceinline__ uint32_t swap16(uint32_t a) { return __byte_perm(a, 0, 0x1032); }
 
+// max of two packed pairs on the FMA pipe instead of the ALU pipe:
+// max(a, b) = b + relu(a - b).  The operands are 16-bit integers 0..255; read
+// as fp16 they are subnormal numbers (k * 2^-24), whose differences and sums
+// below 2^11 are exact in fp16, so the result is the integer maximum bit for
+// bit.  Used for part of the maxima so the two pipes share the work.
+__device__ __forceinline__ uint32_t vmax2_fma(uint32_t a, uint32_t b) {
+  uint32_t t, d;
+  const uint32_t neg1 = 0xBC00BC00u;   // (-1.0, -1.0) in f16x2
+  asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(t) : "r"(b), "r"(neg1), "r"(a));
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(t), "r"(b));
+  return d;
+}
 
 // ---------------------------------------------------------------- geometry
 // LB: lane bits of x (the shuffle offset d runs over them); SB: lane bits that
@@ -63,15 +75,39 @@ template <int Q> struct Geo {
   static constexpr int DC = (DS * XN <= 32) ? DS : 32 / XN;   // steps per B chunk (<= 32 regs)
   static constexpr int OPL = 1 << TB;           // outputs per lane
   static constexpr int W = Q / 2;               // 32-bit words per vector
+  static constexpr int PW = (W + G - 1) / G;    // permutation words per lane
   static constexpr int BPL = Q / G;             // bytes per lane when a group writes q bytes
   static constexpr int VB = (2 * Q + 15) / 16 * 16;  // bytes per 16-bit vector in smem
-  // variable-node pass: VG lanes per variable node, VBPL bytes each
+  // variable-node pass: VG lanes per variable node, VBPL bytes (VBPL/2 packed words) each
   static constexpr int VBPL = Q >= 256 ? 8 : (Q >= 4 ? 4 : 2);
   static constexpr int VG = Q / VBPL;
+  static constexpr int VW = VBPL / 2;
   static_assert(LB >= 1 && TB >= 0 && XB == SB + TB, "layout");
   static_assert(G <= 32 && G * OPL == Q, "group covers the field");
   static_assert(DS % DC == 0, "chunking");
 };
+
+// Of the XN * AWN maxima of one shuffle step, how many use vmax2_fma.
+#ifndef NBLDPC_FMAMAX_64
+#define NBLDPC_FMAMAX_64 6
+#endif
+template <int Q> struct FmaMax { static constexpr int v = Q == 64 ? NBLDPC_FMAMAX_64 : 0; };
+
+// Lane constants of the convolution, computed once per thread.
+struct ConvLane {
+  int a_off;      // word index of the lane's first packed A word
+  uint32_t sel;   // byte_perm selector: identity, or swap of the 16-bit halves on odd lanes
+  int c_off;      // 16-bit index of the lane's first output
+};
+
+template <int Q> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
+  using g = Geo<Q>;
+  ConvLane c;
+  c.a_off = (((s << g::TB) * g::DN) + (l & ~1)) >> 1;
+  c.sel = (l & 1) ? 0x1032u : 0x3210u;
+  c.c_off = (s << g::TB) * g::DN + l;
+  return c;
+}
 
 // ---------------------------------------------------------------- convolution
 // C = A (*) B: C(x) = min_y max(A(y), B(x ^ y)); vectors are q 16-bit values
@@ -80,24 +116,19 @@ template <int Q> struct Geo {
 // register part yr in [s * 2^TB, (s + 1) * 2^TB).  A packed A word pairs the
 // lane positions (l, l ^ 1), so offset d = 2*ds reaches lane positions l ^ d
 // and l ^ d ^ 1 in one shuffle, and the matching B values B(j*DN + d),
-// B(j*DN + d + 1) form one natural 32-bit word whatever the parity of x.
-// Accumulator slot r holds xh = r ^ (s << TB), which makes the B register
-// index r ^ t independent of the lane and lets the final reduce-scatter keep
-// and send fixed slots.  Inputs and output must not alias; the caller syncs
-// the group afterwards.
+// B(j*DN + d + 1) form one natural 32-bit word whatever the parity of x, read
+// by all lanes from the same shared-memory address.  Accumulator slot r holds
+// xh = r ^ (s << TB), which makes the B register index r ^ t independent of
+// the lane and lets the final reduce-scatter keep and send fixed slots.
+// Inputs and output must not alias; the caller syncs the group afterwards.
 template <int Q>
 __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
-                                        uint16_t* __restrict__ C, int s, int l, unsigned gmask) {
+                                        uint16_t* __restrict__ C, const ConvLane& ln, unsigned gmask) {
   using g = Geo<Q>;
   uint32_t aown[g::AWN];
 #pragma unroll
-  for (int t = 0; t < g::AWN; ++t) {
-    const uint32_t w = A[(((s << g::TB) | t) * g::DN + (l & ~1)) >> 1];
-    aown[t] = (l & 1) ? swap16(w) : w;
-  }
+  for (int t = 0; t < g::AWN; ++t) aown[t] = __byte_perm(A[ln.a_off + t * g::DS], 0, ln.sel);
   uint32_t acc[g::XN];
-#pragma unroll
-  for (int x = 0; x < g::XN; ++x) acc[x] = 0xFFFFFFFFu;
 
 #pragma unroll
   for (int c0 = 0; c0 < g::DS; c0 += g::DC) {
@@ -131,7 +162,11 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
 #pragma unroll
       for (int r = 0; r < g::XN; ++r)
 #pragma unroll
-        for (int t = 0; t < g::AWN; ++t) acc[r] = vmin2(acc[r], vmax2(a[t], bl[dd][r ^ t]));
+        for (int t = 0; t < g::AWN; ++t) {
+          const uint32_t m = (r * g::AWN + t < FmaMax<Q>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
+                                                              : vmax2(a[t], bl[dd][r ^ t]);
+          acc[r] = (d == 0 && t == 0) ? m : vmin2(acc[r], m);
+        }
     }
   }
   // reduce-scatter over the SB lane bits: keep slot r, receive the partner's r | 2^c
@@ -143,15 +178,12 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
       acc[r] = vmin2(acc[r], __shfl_xor_sync(gmask, acc[r | (1 << c)], 1 << (g::LB + b)));
   }
 #pragma unroll
-  for (int r = 0; r < g::OPL; ++r) {
-    const uint32_t v = vmin2(acc[r], acc[r] >> 16);
-    C[(((s << g::TB) | r) * g::DN) + l] = (uint16_t)v;
-  }
+  for (int r = 0; r < g::OPL; ++r) C[ln.c_off + r * g::DN] = (uint16_t)vmin2(acc[r], acc[r] >> 16);
 }
 
 // ---------------------------------------------------------------- parameters
 struct CodeBlob {           // offsets (bytes) into the code blob
-  int exp2, log, row_ptr, edge_col, edge_lh, vn_ptr, vn_edge, bytes;
+  int exp2, log, row_ptr, edge_col, edge_lh, edge_lhi, vn_ptr, vn_edge, bytes;
 };
 
 struct DecodeParams {
@@ -167,27 +199,11 @@ struct DecodeParams {
   int n, m, nnz, dmax;
   int frames, max_iters, early_stop;
   int group_bytes;          // per-group shared scratch
+  int key16;                // (255 * (max column degree + 1) + 1) * q <= 65536: 16-bit argmin keys
 };
 
 template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax) {
   return ((dmax * Q + 15) / 16) * 16 + (2 * dmax + 3) * Geo<Q>::VB;
-}
-
-template <int N> __device__ __forceinline__ void load_bytes(const uint8_t* p, int (&v)[N]) {
-  if constexpr (N == 1) {
-    v[0] = *p;
-  } else if constexpr (N == 2) {
-    const uint32_t w = *reinterpret_cast<const uint16_t*>(p);
-    v[0] = w & 0xFF; v[1] = w >> 8;
-  } else if constexpr (N == 4) {
-    const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = (w >> (8 * i)) & 0xFF;
-  } else {
-    const uint2 w = *reinterpret_cast<const uint2*>(p);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { v[i] = (w.x >> (8 * i)) & 0xFF; v[i + 4] = (w.y >> (8 * i)) & 0xFF; }
-  }
 }
 
 template <int N> __device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[N]) {
@@ -202,6 +218,34 @@ template <int N> __device__ __forceinline__ void store_bytes(uint8_t* p, const i
     w.x = (uint32_t)(v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24));
     w.y = (uint32_t)(v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24));
     *reinterpret_cast<uint2*>(p) = w;
+  }
+}
+
+// NB bytes -> NB/2 words of two 16-bit values (byte 2i in the low half of word i)
+template <int NB> __device__ __forceinline__ void load_pairs(const uint8_t* p, uint32_t (&w)[NB / 2]) {
+  if constexpr (NB == 2) {
+    w[0] = __byte_perm(*reinterpret_cast<const uint16_t*>(p), 0, 0x4140);
+  } else if constexpr (NB == 4) {
+    const uint32_t x = *reinterpret_cast<const uint32_t*>(p);
+    w[0] = __byte_perm(x, 0, 0x4140); w[1] = __byte_perm(x, 0, 0x4342);
+  } else {
+    const uint2 x = *reinterpret_cast<const uint2*>(p);
+    w[0] = __byte_perm(x.x, 0, 0x4140); w[1] = __byte_perm(x.x, 0, 0x4342);
+    w[2] = __byte_perm(x.y, 0, 0x4140); w[3] = __byte_perm(x.y, 0, 0x4342);
+  }
+}
+
+// inverse of load_pairs (every 16-bit value must be <= 255)
+template <int NB> __device__ __forceinline__ void store_pairs(uint8_t* p, const uint32_t (&w)[NB / 2]) {
+  if constexpr (NB == 2) {
+    *reinterpret_cast<uint16_t*>(p) = (uint16_t)__byte_perm(w[0], 0, 0x4420);
+  } else if constexpr (NB == 4) {
+    *reinterpret_cast<uint32_t*>(p) = __byte_perm(w[0], w[1], 0x6420);
+  } else {
+    uint2 x;
+    x.x = __byte_perm(w[0], w[1], 0x6420);
+    x.y = __byte_perm(w[2], w[3], 0x6420);
+    *reinterpret_cast<uint2*>(p) = x;
   }
 }
 
@@ -220,10 +264,17 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // ---------------------------------------------------------------- the kernel
+// Resident 256-thread blocks per SM the register allocation must allow: the
+// q >= 128 instances need more than 85 registers per thread without spilling.
+#ifndef NBLDPC_MINB_64
+#define NBLDPC_MINB_64 4
+#endif
+template <int Q> struct MinBlocks { static constexpr int v = Q >= 128 ? 2 : (Q == 64 ? NBLDPC_MINB_64 : 4); };
+
 template <int Q>
-__global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p) {
+__global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const DecodeParams p) {
   using g = Geo<Q>;
-  constexpr int PW = (g::W + g::G - 1) / g::G;   // permutation words per lane
+  constexpr int PW = g::PW;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sblob = smem;
   uint8_t* chat = smem + p.off.bytes;                                    // [n]
@@ -238,7 +289,8 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
   const uint8_t* glog = sblob + p.off.log;         // log_x(v), v >= 1
   const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + p.off.row_ptr);
   const uint16_t* edge_col = reinterpret_cast<const uint16_t*>(sblob + p.off.edge_col);
-  const uint8_t* edge_lh = sblob + p.off.edge_lh;  // log_x(h) of each edge
+  const uint8_t* edge_lh = sblob + p.off.edge_lh;    // log_x(h) of each edge
+  const uint8_t* edge_lhi = sblob + p.off.edge_lhi;  // log_x(h^-1) of each edge
   const uint16_t* vn_ptr = reinterpret_cast<const uint16_t*>(sblob + p.off.vn_ptr);
   const uint16_t* vn_edge = reinterpret_cast<const uint16_t*>(sblob + p.off.vn_edge);
 
@@ -248,16 +300,21 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
   const int grp = tid / g::G, ngroups = blockDim.x / g::G;
   const int gl = tid % g::G;
   const unsigned gmask = group_mask<g::G>(lane);
-  const int s = gl >> g::LB, l = gl & (g::DN - 1);
+  const ConvLane cl = conv_lane<Q>(gl >> g::LB, gl & (g::DN - 1));
   // variable-node groups (VG lanes per variable node)
   const int vgrp = tid / g::VG, nvgroups = blockDim.x / g::VG;
   const int vgl = tid % g::VG;
   const unsigned vmask = group_mask<g::VG>(lane);
+  // symbol values of this lane's packed words in the variable-node pass
+  uint32_t vsym[g::VW];
+#pragma unroll
+  for (int i = 0; i < g::VW; ++i)
+    vsym[i] = (uint32_t)(vgl * g::VBPL + 2 * i) | ((uint32_t)(vgl * g::VBPL + 2 * i + 1) << 16);
 
   // lane constants for the coefficient permutations: logarithms of the
-  // symbols this lane gathers (permutation) and writes (de-permutation); the
-  // zero symbol, which every multiplication fixes, is flagged separately.
-  // Packed 8 bits per symbol (q <= 256 keeps every logarithm below 255).
+  // symbols this lane gathers (permutation) and writes (de-permutation),
+  // packed 8 bits per symbol; the zero symbol, which every multiplication
+  // fixes, is flagged separately.
   uint32_t py_log0 = 0, py_log1 = 0, py_nz0 = 0;   // word i: bits [8i, 8i+8)
 #pragma unroll
   for (int i = 0; i < PW; ++i) {
@@ -283,8 +340,6 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
   // vectors: P_j = vec(j), F_j = vec(dmax + j), B ping-pong = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
   uint8_t* X = p.msg + (size_t)blockIdx.x * p.slot_bytes;
 
-  const int qm1 = Q - 1;
-
   for (;;) {
     if (tid == 0) s_frame = atomicAdd(p.counter, 1u);
     __syncthreads();
@@ -295,36 +350,56 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
     // ---- variable-node pass (Alg. 2, VNP and hard decision):
     //   S(a) = gamma(a) + sum over edges of beta(a);  c = argmin S (lowest a)
     //   alpha_e(a) = min(255, (S - beta_e)(a) - min_b (S - beta_e)(b))
+    // Values are 16-bit halves of 32-bit words: every sum stays below 2^16
+    // (at most 255 * (column degree + 1)), so plain 32-bit adds and
+    // subtractions never carry or borrow across the halves.
     auto vnp = [&](bool first, bool want_alpha) {
       for (int vn = vgrp; vn < p.n; vn += nvgroups) {
-        int S[g::VBPL];
-        load_bytes<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
+        uint32_t S[g::VW];
+        load_pairs<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
         const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
         if (!first) {
           for (int k = k0; k < k1; ++k) {
-            int b[g::VBPL];
-            load_bytes<g::VBPL>(X + (size_t)vn_edge[k] * Q + vgl * g::VBPL, b);
+            uint32_t b[g::VW];
+            load_pairs<g::VBPL>(X + (size_t)vn_edge[k] * Q + vgl * g::VBPL, b);
 #pragma unroll
-            for (int i = 0; i < g::VBPL; ++i) S[i] += b[i];
+            for (int i = 0; i < g::VW; ++i) S[i] += b[i];
           }
         }
-        int key = 0x7FFFFFFF;
+        int key;
+        if (p.key16) {        // key = S * q + a fits 16 bits: minimum value, lowest symbol
+          uint32_t kw = S[0] * (uint32_t)Q + vsym[0];
 #pragma unroll
-        for (int i = 0; i < g::VBPL; ++i) key = min(key, (S[i] << 8) | (vgl * g::VBPL + i));
-        key = group_min<g::VG>(key, vmask);
-        if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
+          for (int i = 1; i < g::VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + vsym[i]);
+          key = (int)min(kw & 0xFFFFu, kw >> 16);
+          key = group_min<g::VG>(key, vmask);
+          if (vgl == 0) chat[vn] = (uint8_t)(key & (Q - 1));
+        } else {
+          key = 0x7FFFFFFF;
+#pragma unroll
+          for (int i = 0; i < g::VW; ++i) {
+            key = min(key, (int)(((S[i] & 0xFFFFu) << 8) | (vsym[i] & 0xFFFFu)));
+            key = min(key, (int)(((S[i] >> 16) << 8) | (vsym[i] >> 16)));
+          }
+          key = group_min<g::VG>(key, vmask);
+          if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
+        }
         if (!first && want_alpha) {
           for (int k = k0; k < k1; ++k) {
             uint8_t* row = X + (size_t)vn_edge[k] * Q + vgl * g::VBPL;
-            int t[g::VBPL];
-            load_bytes<g::VBPL>(row, t);
-            int mn = 0x7FFFFFFF;
+            uint32_t t[g::VW];
+            load_pairs<g::VBPL>(row, t);
 #pragma unroll
-            for (int i = 0; i < g::VBPL; ++i) { t[i] = S[i] - t[i]; mn = min(mn, t[i]); }
+            for (int i = 0; i < g::VW; ++i) t[i] = S[i] - t[i];
+            uint32_t mw = t[0];
+#pragma unroll
+            for (int i = 1; i < g::VW; ++i) mw = vmin2(mw, t[i]);
+            int mn = (int)min(mw & 0xFFFFu, mw >> 16);
             mn = group_min<g::VG>(mn, vmask);
+            const uint32_t mm = (uint32_t)mn * 0x10001u;
 #pragma unroll
-            for (int i = 0; i < g::VBPL; ++i) t[i] = min(255, t[i] - mn);
-            store_bytes<g::VBPL>(row, t);
+            for (int i = 0; i < g::VW; ++i) t[i] = vmin2(t[i] - mm, 0x00FF00FFu);
+            store_pairs<g::VBPL>(row, t);
           }
         }
       }
@@ -366,7 +441,7 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
         group_sync<g::G>(gmask);
         // permutation: P_j(y) = alpha_j(h_j^-1 y), 16-bit natural order
         for (int j = 0; j < d; ++j) {
-          const int lhinv = (qm1 - edge_lh[e0 + j]) % qm1;
+          const int lhinv = edge_lhi[e0 + j];
           const uint8_t* a = stage + j * Q;
           uint32_t* P = vec(j);
 #pragma unroll
@@ -385,13 +460,14 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
           const int lh = edge_lh[e];
           int out[g::BPL];
 #pragma unroll
-          for (int i = 0; i < g::BPL; ++i) out[i] = R16[(da_mask >> i) & 1 ? exp2[((da_log >> (8 * i)) & 0xFF) + lh] : 0];
+          for (int i = 0; i < g::BPL; ++i)
+            out[i] = R16[(da_mask >> i) & 1 ? exp2[((da_log >> (8 * i)) & 0xFF) + lh] : 0];
           store_bytes<g::BPL>(X + (size_t)e * Q + gl * g::BPL, out);
         };
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
         int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<Q>(vec(fprev), vec(j), vec16(p.dmax + j), s, l, gmask);
+          mm_conv<Q>(vec(fprev), vec(j), vec16(p.dmax + j), cl, gmask);
           group_sync<g::G>(gmask);
           fprev = p.dmax + j;
         }
@@ -402,11 +478,11 @@ __global__ void __launch_bounds__(256, 2) mma_decode_kernel(const DecodeParams p
         for (int j = d - 2; j >= 1; --j) {
           const int fj = (j == 1) ? 0 : p.dmax + j - 1;
           const int rv = 2 * p.dmax + 2;
-          mm_conv<Q>(vec(fj), vec(bcur), vec16(rv), s, l, gmask);
+          mm_conv<Q>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
           group_sync<g::G>(gmask);
           depermute(vec16(rv), e0 + j);
           const int bn = 2 * p.dmax + pp;
-          mm_conv<Q>(vec(bcur), vec(j), vec16(bn), s, l, gmask);
+          mm_conv<Q>(vec(bcur), vec(j), vec16(bn), cl, gmask);
           group_sync<g::G>(gmask);
           bcur = bn;
           pp ^= 1;

@@ -27,7 +27,7 @@ struct LaunchCfg {
 }  // namespace
 
 struct nbldpc_code {
-  int q = 0, p = 0, n = 0, m = 0, nnz = 0, dmax = 0;
+  int q = 0, p = 0, n = 0, m = 0, nnz = 0, dmax = 0, vmax = 0;
   uint32_t poly = 0;
   int device = 0;
   unsigned char* blob_dev = nullptr;
@@ -172,6 +172,7 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
   prm.max_iters = max_iters;
   prm.early_stop = early_stop ? 1 : 0;
   prm.group_bytes = c->cfg.group_bytes;
+  prm.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
   const int grid = grid_for(c, frames);
@@ -226,6 +227,7 @@ int launch_noalloc(const nbldpc_code* c, const uint8_t* gamma, int frames, int m
   prm.max_iters = max_iters;
   prm.early_stop = early_stop ? 1 : 0;
   prm.group_bytes = c->cfg.group_bytes;
+  prm.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
   // the array keeps the previous call's contents: the frame counter must start at zero
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
@@ -310,7 +312,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   }
   if (dmax > 64 || vmax > 64) return NBLDPC_ERR_UNSUPPORTED;
 
-  // code blob: exp2 | log | row_ptr u16 | edge_col u16 | edge_lh u8 | vn_ptr u16 | vn_edge u16
+  // code blob: exp2 | log | row_ptr u16 | edge_col u16 | edge_lh u8 | edge_lhi u8 | vn_ptr u16 | vn_edge u16
   nbldpc::CodeBlob off{};
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = o; o = round_up(o + bytes, 16); return (int)at; };
@@ -319,6 +321,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   off.row_ptr = take(2 * ((size_t)n_rows + 1));
   off.edge_col = take(2 * (size_t)nnz);
   off.edge_lh = take((size_t)nnz);
+  off.edge_lhi = take((size_t)nnz);
   off.vn_ptr = take(2 * ((size_t)n_cols + 1));
   off.vn_edge = take(2 * (size_t)nnz);
   off.bytes = (int)o;
@@ -328,12 +331,14 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   uint16_t* rp = reinterpret_cast<uint16_t*>(&blob[off.row_ptr]);
   uint16_t* ec = reinterpret_cast<uint16_t*>(&blob[off.edge_col]);
   uint8_t* elh = &blob[off.edge_lh];
+  uint8_t* elhi = &blob[off.edge_lhi];
   uint16_t* vp = reinterpret_cast<uint16_t*>(&blob[off.vn_ptr]);
   uint16_t* ve = reinterpret_cast<uint16_t*>(&blob[off.vn_edge]);
   for (int r = 0; r <= n_rows; ++r) rp[r] = (uint16_t)row_ptr[r];
   for (int e = 0; e < nnz; ++e) {
     ec[e] = (uint16_t)col_idx[e];
     elh[e] = lg[coef[e]];
+    elhi[e] = (uint8_t)((q - 1 - lg[coef[e]]) % (q - 1));
   }
   vp[0] = 0;
   for (int c = 0; c < n_cols; ++c) vp[c + 1] = (uint16_t)(vp[c] + vdeg[c]);
@@ -352,6 +357,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   c->m = n_rows;
   c->nnz = nnz;
   c->dmax = dmax;
+  c->vmax = vmax;
   c->poly = prim_poly;
   c->off = off;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return NBLDPC_ERR_CUDA; }
