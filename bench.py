@@ -70,7 +70,7 @@ def dist_setup(args):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("mma_kernels.cuh", "nbldpc.cu"):
+    for f in ("mma_kernels.cuh",):
         with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
