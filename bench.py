@@ -33,7 +33,11 @@ import torch  # noqa: E402
 
 WORKLOAD = "gf64_n576_dv2_dc4"
 SM_COUNT = 152
-PEAK_OPS_PER_CLK_SM = 4 * 16 * 2   # ALU pipe: 4 sub-partitions x 16 lanes/clk x 2 halves of u16x2 min/max
+# Issue-bound min/max ceiling: an SM issues 4 warp instructions per clock; a
+# min-max pair costs at best one instruction per lane per two 16-bit pairs
+# (max on the ALU or, as relu(a-b)+b, on the FMA pipe; 3-input min on the ALU),
+# i.e. 128 pairs = 256 16-bit min/max ops per clock per SM.
+PEAK_OPS_PER_CLK_SM = 256
 SM_MAX_MHZ_FALLBACK = 2070.0
 
 
@@ -280,7 +284,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops,
                      "traffic": None if bpf is None else bpf * frames,
-                     "peak_kind": f"derived: 152 SMs x 128 u16 min/max ops/clk (ALU pipe) x {mhz:.0f} MHz ({mhz_kind} max SM clock)"},
+                     "peak_kind": f"derived: 152 SMs x 256 u16 min/max ops/clk (issue-bound ALU+FMA mix) x {mhz:.0f} MHz ({mhz_kind} max SM clock)"},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,
