@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=None, help="frames per Eb/N0 point (default: 65536)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default layout / frames per block")
     return ap.parse_args()
 
 
@@ -210,6 +211,13 @@ def main():
     gamma = make_inputs(code, w, fpp, dev, rank)
     frames = gamma.shape[0]
     dec = binding.Decoder.from_code(code)
+    tuning = {"source": "default"}
+    if not args.no_autotune:
+        # time every (layout variant, frames per block) pair on 4096 of the step's frames, fixed 3 iterations
+        res = dec.autotune(gamma[: min(frames, 4096)], 3)
+        tuning = {"source": "autotuned", "candidates_ms": {f"v{v}_fpb{f}": round(ms, 3) for v, f, ms in res}}
+    v, fpb = dec.tuning()
+    tuning.update({"variant": v, "frames_per_block": fpb})
     stream = torch.cuda.Stream(device=dev)
     sym = torch.empty((frames, code.n), dtype=torch.uint8, device=dev)
     its = torch.empty((frames,), dtype=torch.int32, device=dev)
@@ -280,7 +288,7 @@ def main():
         "config": {"workload": WORKLOAD, "frames_per_step": frames, "q": code.q, "n": code.n,
                    "k": code.k, "dv": w["dv"], "dc": w["dc"], "ebn0_db": list(w["ebn0"]),
                    "max_iters": mi, "early_stop": bool(es), "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"frames sharded over {ws} GPU(s)"},
+                   "parallelism": f"frames sharded over {ws} GPU(s)", "tuning": tuning},
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops,
                      "traffic": None if bpf is None else bpf * frames,

@@ -138,6 +138,83 @@ int nbldpc_decode_host(const nbldpc_code *code, const uint8_t *gamma_host, int f
                        size_t workspace_bytes, void *cuda_stream);
 
 /*
+ * ---- Mixed-code batches -------------------------------------------------
+ * One persistent launch decodes the frames of up to NBLDPC_MAX_BATCH_JOBS
+ * jobs, each with its own code (any q, N, degrees), reliabilities, iteration
+ * limit and outputs.  The frames of all jobs form one work list; a block
+ * slot takes the next frame as soon as its previous one has stopped (zero
+ * syndrome or max_iters), so codes with different frame counts and frames
+ * with different iteration counts share the GPU without idle tails.  Results
+ * are identical to nbldpc_decode of each job on its own (frames are
+ * independent); only the throughput differs.  The launch is a counter reset
+ * plus one kernel on the caller's stream, so it can be captured in a CUDA
+ * graph and replayed (same buffers) without host work.  This is the batching
+ * form of the paper's multicodeword mapping (Sec. 4: one frame per processing
+ * unit, no synchronization between frames), extended to mixed codes.
+ */
+#define NBLDPC_MAX_BATCH_JOBS 8
+
+typedef struct nbldpc_job {
+  const nbldpc_code *code;  /* all codes of a batch on the same device */
+  const uint8_t *gamma_dev; /* [frames][n][q], 16-byte aligned */
+  int frames;               /* >= 0 */
+  int max_iters;            /* >= 0 */
+  int early_stop;
+  uint8_t *out_sym_dev;     /* [frames][n] */
+  int32_t *out_iters_dev;   /* [frames] */
+  uint8_t *out_ok_dev;      /* [frames] */
+} nbldpc_job;
+
+/* Device workspace for nbldpc_decode_batch with these jobs (their codes' current tuning). */
+int nbldpc_decode_batch_workspace_size(const nbldpc_job *jobs, int n_jobs, size_t *bytes);
+
+/*
+ * Queue the batch on `cuda_stream`.  Each code decodes with its own layout
+ * variant; the block is split into the smallest frames-per-block value among
+ * the jobs' codes.  Errors: NBLDPC_ERR_ARG (n_jobs outside [1,
+ * NBLDPC_MAX_BATCH_JOBS], bad pointers, short workspace), NBLDPC_ERR_UNSUPPORTED
+ * (the combined shared-memory need exceeds the device), NBLDPC_ERR_CUDA.
+ */
+int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev, size_t workspace_bytes,
+                        void *cuda_stream);
+
+/*
+ * ---- Tuning ----------------------------------------------------------------
+ * Two knobs per code change speed, never results: the layout variant (0 or
+ * 1: how the q x q min-max work of one convolution is split between the lanes
+ * of a group and their registers) and the frames decoded side by side in one
+ * 256-thread block (1, 2, 4 or 8; small codes leave threads idle at 1).
+ * nbldpc_code_create picks variant 0 and a frames-per-block value from the
+ * code size; nbldpc_code_autotune measures every valid pair on the caller's
+ * frames and keeps the fastest.
+ */
+typedef struct nbldpc_tune_result {
+  int variant;
+  int frames_per_block;
+  float ms;                 /* time of one decode of the tuning frames, fixed iterations */
+} nbldpc_tune_result;
+
+int nbldpc_code_get_tuning(const nbldpc_code *code, int *variant, int *frames_per_block);
+
+/* Set the tuning by hand; NBLDPC_ERR_UNSUPPORTED if that pair does not fit the device. */
+int nbldpc_code_set_tuning(nbldpc_code *code, int variant, int frames_per_block);
+
+/* Device workspace nbldpc_code_autotune needs for `frames` tuning frames. */
+int nbldpc_code_autotune_workspace_size(const nbldpc_code *code, int frames, size_t *bytes);
+
+/*
+ * Time a fixed-iteration decode (max_iters >= 1, no early stop) of the
+ * caller's `frames` frames gamma_dev for every valid (variant,
+ * frames-per-block) pair, keep the fastest, and report each measurement in
+ * results[0 .. min(max_results, *n_results)).  Synchronous: returns after the
+ * measurements (it waits on `cuda_stream`).  Not thread safe with respect to
+ * other calls on the same handle.
+ */
+int nbldpc_code_autotune(nbldpc_code *code, const uint8_t *gamma_dev, int frames, int max_iters,
+                         void *workspace_dev, size_t workspace_bytes, void *cuda_stream,
+                         nbldpc_tune_result *results, int max_results, int *n_results);
+
+/*
  * Size of the fixed device array that nbldpc_decode_noalloc works in.
  */
 #define NBLDPC_NOALLOC_SCRATCH_BYTES (32u << 20)

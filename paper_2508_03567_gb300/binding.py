@@ -28,8 +28,22 @@ NBLDPC_ERR_UNSUPPORTED = -7
 
 EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_workspace_size", "nbldpc_decode", "nbldpc_decode_host_workspace_size",
-            "nbldpc_decode_host", "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
+            "nbldpc_decode_host", "nbldpc_decode_batch_workspace_size", "nbldpc_decode_batch",
+            "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
+            "nbldpc_code_autotune", "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
+
+NBLDPC_MAX_BATCH_JOBS = 8
+
+
+class nbldpc_job(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("gamma_dev", ctypes.c_void_p), ("frames", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("early_stop", ctypes.c_int), ("out_sym_dev", ctypes.c_void_p),
+                ("out_iters_dev", ctypes.c_void_p), ("out_ok_dev", ctypes.c_void_p)]
+
+
+class nbldpc_tune_result(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("frames_per_block", ctypes.c_int), ("ms", ctypes.c_float)]
 
 _lib = None
 _lock = threading.Lock()
@@ -66,6 +80,15 @@ def lib() -> ctypes.CDLL:
                                              vp, ctypes.c_int, vp, sz, vp]
             L.nbldpc_decode_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                                 vp, vp]
+            jp = ctypes.POINTER(nbldpc_job)
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.nbldpc_decode_batch_workspace_size.argtypes = [jp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_decode_batch.argtypes = [jp, ctypes.c_int, vp, sz, vp]
+            L.nbldpc_code_get_tuning.argtypes = [vp, ip, ip]
+            L.nbldpc_code_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
+                                               ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]
             L.nbldpc_kernel_launch_count.argtypes = []
             L.nbldpc_kernel_launch_count.restype = ctypes.c_uint64
             L.nbldpc_status_string.argtypes = [ctypes.c_int]
@@ -177,6 +200,66 @@ def nbldpc_decode_noalloc(handle: int, gamma, frames: int, max_iters: int, early
     _check(st, "nbldpc_decode_noalloc")
 
 
+def _jobs_array(jobs):
+    arr = (nbldpc_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        if isinstance(j, dict):
+            j = (j["code"], j["gamma"], j["frames"], j["max_iters"], j["early_stop"], j["out_sym"],
+                 j["out_iters"], j["out_ok"])
+        code, gamma, frames, mi, es, sym, its, ok = j
+        arr[i] = nbldpc_job(code, _ptr(gamma), int(frames), int(mi), int(es), _ptr(sym), _ptr(its), _ptr(ok))
+    return arr
+
+
+def nbldpc_decode_batch_workspace_size(jobs) -> int:
+    """Workspace bytes for a batch; jobs: sequence of (handle, gamma, frames, max_iters, early_stop,
+    out_sym, out_iters, out_ok) tuples or dicts with those keys."""
+    arr = _jobs_array(jobs)
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_decode_batch_workspace_size(arr, len(jobs), ctypes.byref(b)),
+           "nbldpc_decode_batch_workspace_size")
+    return b.value
+
+
+def nbldpc_decode_batch(jobs, workspace, workspace_bytes: int | None = None, stream=None) -> None:
+    """Queue one persistent launch over the frames of every job (mixed codes)."""
+    arr = _jobs_array(jobs)
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().nbldpc_decode_batch(arr, len(jobs), _ptr(workspace), int(workspace_bytes), _stream_ptr(stream)),
+           "nbldpc_decode_batch")
+
+
+def nbldpc_code_get_tuning(handle: int):
+    v, f = ctypes.c_int(), ctypes.c_int()
+    _check(lib().nbldpc_code_get_tuning(handle, ctypes.byref(v), ctypes.byref(f)), "nbldpc_code_get_tuning")
+    return v.value, f.value
+
+
+def nbldpc_code_set_tuning(handle: int, variant: int, frames_per_block: int) -> None:
+    _check(lib().nbldpc_code_set_tuning(handle, int(variant), int(frames_per_block)), "nbldpc_code_set_tuning")
+
+
+def nbldpc_code_autotune_workspace_size(handle: int, frames: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_code_autotune_workspace_size(handle, int(frames), ctypes.byref(b)),
+           "nbldpc_code_autotune_workspace_size")
+    return b.value
+
+
+def nbldpc_code_autotune(handle: int, gamma, frames: int, max_iters: int, workspace,
+                         workspace_bytes: int | None = None, stream=None):
+    """Measure every (variant, frames-per-block) pair, keep the fastest; returns the measurements."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    res = (nbldpc_tune_result * 16)()
+    n = ctypes.c_int()
+    _check(lib().nbldpc_code_autotune(handle, _ptr(gamma), int(frames), int(max_iters), _ptr(workspace),
+                                      int(workspace_bytes), _stream_ptr(stream), res, 16, ctypes.byref(n)),
+           "nbldpc_code_autotune")
+    return [(res[i].variant, res[i].frames_per_block, res[i].ms) for i in range(min(n.value, 16))]
+
+
 class Decoder:
     """Owns a code handle; allocates outputs and workspace with torch."""
 
@@ -199,6 +282,18 @@ class Decoder:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, gamma: torch.Tensor, max_iters: int, frames: int | None = None):
+        f = gamma.shape[0] if frames is None else frames
+        ws = torch.empty(nbldpc_code_autotune_workspace_size(self.handle, f), dtype=torch.uint8,
+                         device=gamma.device)
+        return nbldpc_code_autotune(self.handle, gamma, f, max_iters, ws)
+
+    def tuning(self):
+        return nbldpc_code_get_tuning(self.handle)
+
+    def set_tuning(self, variant: int, frames_per_block: int) -> None:
+        nbldpc_code_set_tuning(self.handle, variant, frames_per_block)
 
     def workspace(self, frames: int, device) -> torch.Tensor:
         need = nbldpc_decode_workspace_size(self.handle, frames)

@@ -49,22 +49,33 @@ __device__ __forceinline__ uint32_t vmax2_fma(uint32_t a, uint32_t b) {
 // ---------------------------------------------------------------- geometry
 // LB: lane bits of x (the shuffle offset d runs over them); SB: lane bits that
 // split the register part of y between lanes.  XB = p - LB register bits of x
-// per lane, TB = XB - SB register bits of y per lane.
-template <int Q> struct Layout;
-template <> struct Layout<2>   { static constexpr int LB = 1, SB = 0; };
-template <> struct Layout<4>   { static constexpr int LB = 1, SB = 0; };
-template <> struct Layout<8>   { static constexpr int LB = 1, SB = 1; };
-template <> struct Layout<16>  { static constexpr int LB = 2, SB = 1; };
-template <> struct Layout<32>  { static constexpr int LB = 2, SB = 2; };
-template <> struct Layout<64>  { static constexpr int LB = 3, SB = 2; };
-template <> struct Layout<128> { static constexpr int LB = 4, SB = 1; };
-template <> struct Layout<256> { static constexpr int LB = 5, SB = 0; };
+// per lane, TB = XB - SB register bits of y per lane.  Each field order has
+// two layouts (variant 0 and 1: two ways of splitting the q x q work between
+// the lanes of a group and their registers); the autotuner picks one per code.
+template <int Q, int V> struct Layout;
+template <> struct Layout<2, 0>   { static constexpr int LB = 1, SB = 0; };
+template <> struct Layout<2, 1>   { static constexpr int LB = 1, SB = 0; };
+template <> struct Layout<4, 0>   { static constexpr int LB = 1, SB = 0; };
+template <> struct Layout<4, 1>   { static constexpr int LB = 2, SB = 0; };
+template <> struct Layout<8, 0>   { static constexpr int LB = 1, SB = 1; };
+template <> struct Layout<8, 1>   { static constexpr int LB = 2, SB = 0; };
+template <> struct Layout<16, 0>  { static constexpr int LB = 2, SB = 1; };
+template <> struct Layout<16, 1>  { static constexpr int LB = 3, SB = 0; };
+template <> struct Layout<32, 0>  { static constexpr int LB = 2, SB = 2; };
+template <> struct Layout<32, 1>  { static constexpr int LB = 3, SB = 1; };
+template <> struct Layout<64, 0>  { static constexpr int LB = 3, SB = 2; };
+template <> struct Layout<64, 1>  { static constexpr int LB = 4, SB = 1; };
+template <> struct Layout<128, 0> { static constexpr int LB = 4, SB = 1; };
+template <> struct Layout<128, 1> { static constexpr int LB = 5, SB = 0; };
+template <> struct Layout<256, 0> { static constexpr int LB = 5, SB = 0; };
+template <> struct Layout<256, 1> { static constexpr int LB = 4, SB = 1; };
 
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
-template <int Q> struct Geo {
+template <int Q_, int V_> struct Geo {
+  static constexpr int Q = Q_, V = V_;
   static constexpr int P = ilog2(Q);
-  static constexpr int LB = Layout<Q>::LB, SB = Layout<Q>::SB;
+  static constexpr int LB = Layout<Q, V>::LB, SB = Layout<Q, V>::SB;
   static constexpr int XB = P - LB;             // register bits of x
   static constexpr int TB = XB - SB;            // register bits of y
   static constexpr int G = 1 << (LB + SB);      // lanes per convolution group
@@ -72,7 +83,7 @@ template <int Q> struct Geo {
   static constexpr int DS = DN / 2;             // shuffle steps (even offsets d = 2*ds)
   static constexpr int XN = 1 << XB;            // accumulators per lane
   static constexpr int AWN = 1 << TB;           // packed A words per lane
-  static constexpr int DC = (DS * XN <= 32) ? DS : 32 / XN;   // steps per B chunk (<= 32 regs)
+  static constexpr int DC = (DS * XN <= 32) ? DS : (32 / XN >= 1 ? 32 / XN : 1);  // steps per B chunk
   static constexpr int OPL = 1 << TB;           // outputs per lane
   static constexpr int W = Q / 2;               // 32-bit words per vector
   static constexpr int PW = (W + G - 1) / G;    // permutation words per lane
@@ -85,6 +96,7 @@ template <int Q> struct Geo {
   static_assert(LB >= 1 && TB >= 0 && XB == SB + TB, "layout");
   static_assert(G <= 32 && G * OPL == Q, "group covers the field");
   static_assert(DS % DC == 0, "chunking");
+  static_assert(BPL == 1 || BPL == 2 || BPL == 4 || BPL == 8, "byte lanes");
 };
 
 // Of the XN * AWN maxima of one shuffle step, how many use vmax2_fma.
@@ -100,8 +112,7 @@ struct ConvLane {
   int c_off;      // 16-bit index of the lane's first output
 };
 
-template <int Q> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
-  using g = Geo<Q>;
+template <class g> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
   ConvLane c;
   c.a_off = (((s << g::TB) * g::DN) + (l & ~1)) >> 1;
   c.sel = (l & 1) ? 0x1032u : 0x3210u;
@@ -121,10 +132,9 @@ template <int Q> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
 // xh = r ^ (s << TB), which makes the B register index r ^ t independent of
 // the lane and lets the final reduce-scatter keep and send fixed slots.
 // Inputs and output must not alias; the caller syncs the group afterwards.
-template <int Q>
+template <class g>
 __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
                                         uint16_t* __restrict__ C, const ConvLane& ln, unsigned gmask) {
-  using g = Geo<Q>;
   uint32_t aown[g::AWN];
 #pragma unroll
   for (int t = 0; t < g::AWN; ++t) aown[t] = __byte_perm(A[ln.a_off + t * g::DS], 0, ln.sel);
@@ -163,7 +173,7 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
       for (int r = 0; r < g::XN; ++r)
 #pragma unroll
         for (int t = 0; t < g::AWN; ++t) {
-          const uint32_t m = (r * g::AWN + t < FmaMax<Q>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
+          const uint32_t m = (r * g::AWN + t < FmaMax<g::Q>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
                                                               : vmax2(a[t], bl[dd][r ^ t]);
           acc[r] = (d == 0 && t == 0) ? m : vmin2(acc[r], m);
         }
@@ -186,24 +196,56 @@ struct CodeBlob {           // offsets (bytes) into the code blob
   int exp2, log, row_ptr, edge_col, edge_lh, edge_lhi, vn_ptr, vn_edge, bytes;
 };
 
-struct DecodeParams {
-  const uint8_t* gamma;     // [frames][n][q]
-  uint8_t* out_sym;         // [frames][n]
-  int32_t* out_iters;       // [frames]
-  uint8_t* out_ok;          // [frames]
-  uint8_t* msg;             // per-block message slots
-  unsigned int* counter;    // next frame
-  const unsigned char* blob;
+// One code and the frames to decode with it.
+struct JobDesc {
+  const unsigned char* blob;  // code description (device)
   CodeBlob off;
-  size_t slot_bytes;
-  int n, m, nnz, dmax;
+  const uint8_t* gamma;       // [frames][n][q]
+  uint8_t* out_sym;           // [frames][n]
+  int32_t* out_iters;         // [frames]
+  uint8_t* out_ok;            // [frames]
+  int q, n, m, dmax;
+  int variant;                // layout variant (0 or 1)
+  int key16;                  // (255 * (max column degree + 1) + 1) * q <= 65536: 16-bit argmin keys
+  int group_bytes;            // per-group shared scratch for this code
   int frames, max_iters, early_stop;
-  int group_bytes;          // per-group shared scratch
-  int key16;                // (255 * (max column degree + 1) + 1) * q <= 65536: 16-bit argmin keys
+  int item_begin;             // index of this job's first frame in the launch's work list
 };
 
+constexpr int kMaxJobs = 8;
+
+// One launch: up to kMaxJobs jobs whose frames form one work list, served by
+// persistent blocks of `fpb` frame slots each.
+struct LaunchParams {
+  JobDesc jobs[kMaxJobs];
+  int njobs, total_items;
+  unsigned int* counter;      // next work item
+  uint8_t* msg;               // message slots, one per (block, frame slot)
+  size_t slot_bytes;
+  int fpb;                    // frame slots per block (blockDim / fpb threads each)
+  int slot_smem;              // shared bytes per frame slot
+  int blob_cap, n_cap;        // largest code blob and N among the jobs
+};
+
+template <int Q> __host__ __device__ constexpr int vec_bytes() { return (2 * Q + 15) / 16 * 16; }
+
 template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax) {
-  return ((dmax * Q + 15) / 16) * 16 + (2 * dmax + 3) * Geo<Q>::VB;
+  return ((dmax * Q + 15) / 16) * 16 + (2 * dmax + 3) * vec_bytes<Q>();
+}
+
+// named barrier over the threads of one frame slot (ids 1..fpb)
+__device__ __forceinline__ void slot_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ int slot_sync_or(int id, int nthreads, int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r;
 }
 
 template <int N> __device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[N]) {
@@ -263,47 +305,34 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
   return (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// ---------------------------------------------------------------- the kernel
-// Resident 256-thread blocks per SM the register allocation must allow: the
-// q >= 128 instances need more than 85 registers per thread without spilling.
-#ifndef NBLDPC_MINB_64
-#define NBLDPC_MINB_64 4
-#endif
-template <int Q> struct MinBlocks { static constexpr int v = Q >= 128 ? 2 : (Q == 64 ? NBLDPC_MINB_64 : 4); };
-
-template <int Q>
-__global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const DecodeParams p) {
-  using g = Geo<Q>;
+// ---------------------------------------------------------------- one frame
+// Decodes frame `frame` of `job` with the nthr threads of one frame slot
+// (slot thread index stid, named barrier bar_id).  sblob holds the job's code
+// description, chat[n] the decisions, scratch the per-group buffers; X is the
+// slot's message area ([nnz][q] bytes).
+template <class g>
+__device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
+                                             uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
+  constexpr int Q = g::Q;
   constexpr int PW = g::PW;
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* sblob = smem;
-  uint8_t* chat = smem + p.off.bytes;                                    // [n]
-  __shared__ unsigned int s_frame;
-  unsigned char* scratch_base = smem + p.off.bytes + ((p.n + 15) / 16) * 16;
+  const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
+  const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
+  const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.row_ptr);
+  const uint16_t* edge_col = reinterpret_cast<const uint16_t*>(sblob + job.off.edge_col);
+  const uint8_t* edge_lh = sblob + job.off.edge_lh;    // log_x(h) of each edge
+  const uint8_t* edge_lhi = sblob + job.off.edge_lhi;  // log_x(h^-1) of each edge
+  const uint16_t* vn_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_ptr);
+  const uint16_t* vn_edge = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_edge);
 
-  // stage the code description (GF tables, H, variable-node view)
-  for (int i = threadIdx.x; i < p.off.bytes / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(sblob)[i] = reinterpret_cast<const uint4*>(p.blob)[i];
-  __syncthreads();
-  const uint8_t* exp2 = sblob + p.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
-  const uint8_t* glog = sblob + p.off.log;         // log_x(v), v >= 1
-  const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + p.off.row_ptr);
-  const uint16_t* edge_col = reinterpret_cast<const uint16_t*>(sblob + p.off.edge_col);
-  const uint8_t* edge_lh = sblob + p.off.edge_lh;    // log_x(h) of each edge
-  const uint8_t* edge_lhi = sblob + p.off.edge_lhi;  // log_x(h^-1) of each edge
-  const uint16_t* vn_ptr = reinterpret_cast<const uint16_t*>(sblob + p.off.vn_ptr);
-  const uint16_t* vn_edge = reinterpret_cast<const uint16_t*>(sblob + p.off.vn_edge);
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  const int lane = threadIdx.x & 31;
   // check-node groups (G lanes per check)
-  const int grp = tid / g::G, ngroups = blockDim.x / g::G;
-  const int gl = tid % g::G;
+  const int grp = stid / g::G, ngroups = nthr / g::G;
+  const int gl = stid % g::G;
   const unsigned gmask = group_mask<g::G>(lane);
-  const ConvLane cl = conv_lane<Q>(gl >> g::LB, gl & (g::DN - 1));
+  const ConvLane cl = conv_lane<g>(gl >> g::LB, gl & (g::DN - 1));
   // variable-node groups (VG lanes per variable node)
-  const int vgrp = tid / g::VG, nvgroups = blockDim.x / g::VG;
-  const int vgl = tid % g::VG;
+  const int vgrp = stid / g::VG, nvgroups = nthr / g::VG;
+  const int vgl = stid % g::VG;
   const unsigned vmask = group_mask<g::VG>(lane);
   // symbol values of this lane's packed words in the variable-node pass
   uint32_t vsym[g::VW];
@@ -332,20 +361,13 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
     if (a) { da_log |= (uint64_t)glog[a] << (8 * i); da_mask |= 1u << i; }
   }
 
-  unsigned char* gs = scratch_base + (size_t)grp * p.group_bytes;
+  unsigned char* gs = scratch + (size_t)grp * job.group_bytes;
   uint8_t* stage = gs;                                                   // [dmax][q] bytes
-  unsigned char* vecs = gs + ((p.dmax * Q + 15) / 16) * 16;
+  unsigned char* vecs = gs + ((job.dmax * Q + 15) / 16) * 16;
   auto vec = [&](int i) { return reinterpret_cast<uint32_t*>(vecs + (size_t)i * g::VB); };
   auto vec16 = [&](int i) { return reinterpret_cast<uint16_t*>(vecs + (size_t)i * g::VB); };
   // vectors: P_j = vec(j), F_j = vec(dmax + j), B ping-pong = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
-  uint8_t* X = p.msg + (size_t)blockIdx.x * p.slot_bytes;
-
-  for (;;) {
-    if (tid == 0) s_frame = atomicAdd(p.counter, 1u);
-    __syncthreads();
-    const int frame = (int)s_frame;
-    if (frame >= p.frames) break;
-    const uint8_t* gam = p.gamma + (size_t)frame * p.n * Q;
+  const uint8_t* gam = job.gamma + (size_t)frame * job.n * Q;
 
     // ---- variable-node pass (Alg. 2, VNP and hard decision):
     //   S(a) = gamma(a) + sum over edges of beta(a);  c = argmin S (lowest a)
@@ -354,7 +376,7 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
     // (at most 255 * (column degree + 1)), so plain 32-bit adds and
     // subtractions never carry or borrow across the halves.
     auto vnp = [&](bool first, bool want_alpha) {
-      for (int vn = vgrp; vn < p.n; vn += nvgroups) {
+      for (int vn = vgrp; vn < job.n; vn += nvgroups) {
         uint32_t S[g::VW];
         load_pairs<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
         const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
@@ -367,7 +389,7 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
           }
         }
         int key;
-        if (p.key16) {        // key = S * q + a fits 16 bits: minimum value, lowest symbol
+        if (job.key16) {        // key = S * q + a fits 16 bits: minimum value, lowest symbol
           uint32_t kw = S[0] * (uint32_t)Q + vsym[0];
 #pragma unroll
           for (int i = 1; i < g::VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + vsym[i]);
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
     // ---- syndrome of chat over all checks (block-wide)
     auto syndrome_ok = [&]() -> bool {
       int bad = 0;
-      for (int r = tid; r < p.m; r += blockDim.x) {
+      for (int r = stid; r < job.m; r += nthr) {
         int sy = 0;
         for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
           const int c = chat[edge_col[e]];
@@ -416,12 +438,12 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
         }
         bad |= sy;
       }
-      return __syncthreads_or(bad) == 0;
+      return slot_sync_or(bar_id, nthr, bad) == 0;
     };
 
     // ---- check-node pass (Alg. 2, F & B matrices and beta), one group per check
     auto cnp = [&](bool first) {
-      for (int r = grp; r < p.m; r += ngroups) {
+      for (int r = grp; r < job.m; r += ngroups) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
         // stage incoming alpha rows (alpha^(0) = gamma on the first pass)
         if constexpr (Q >= 16) {
@@ -467,22 +489,22 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
         int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<Q>(vec(fprev), vec(j), vec16(p.dmax + j), cl, gmask);
+          mm_conv<g>(vec(fprev), vec(j), vec16(job.dmax + j), cl, gmask);
           group_sync<g::G>(gmask);
-          fprev = p.dmax + j;
+          fprev = job.dmax + j;
         }
         depermute(vec16(fprev), e0 + d - 1);               // beta_{d-1} from F_{d-2}
         // backward: B_{d-1} = P_{d-1}; beta_j from F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j
         int bcur = d - 1;
         int pp = 0;
         for (int j = d - 2; j >= 1; --j) {
-          const int fj = (j == 1) ? 0 : p.dmax + j - 1;
-          const int rv = 2 * p.dmax + 2;
-          mm_conv<Q>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
+          const int fj = (j == 1) ? 0 : job.dmax + j - 1;
+          const int rv = 2 * job.dmax + 2;
+          mm_conv<g>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
           group_sync<g::G>(gmask);
           depermute(vec16(rv), e0 + j);
-          const int bn = 2 * p.dmax + pp;
-          mm_conv<Q>(vec(bcur), vec(j), vec16(bn), cl, gmask);
+          const int bn = 2 * job.dmax + pp;
+          mm_conv<g>(vec(bcur), vec(j), vec16(bn), cl, gmask);
           group_sync<g::G>(gmask);
           bcur = bn;
           pp ^= 1;
@@ -494,26 +516,100 @@ __global__ void __launch_bounds__(256, MinBlocks<Q>::v) mma_decode_kernel(const 
 
     // ---- decode one frame
     vnp(true, false);                // c^(0) = argmin gamma
-    __syncthreads();
+    slot_sync(bar_id, nthr);
     bool ok = syndrome_ok();
     int iters = 0;
-    if (!(p.early_stop && ok)) {
-      for (int k = 1; k <= p.max_iters; ++k) {
+    if (!(job.early_stop && ok)) {
+      for (int k = 1; k <= job.max_iters; ++k) {
         cnp(k == 1);
-        __syncthreads();
-        vnp(false, k < p.max_iters);
-        __syncthreads();
+        slot_sync(bar_id, nthr);
+        vnp(false, k < job.max_iters);
+        slot_sync(bar_id, nthr);
         iters = k;
         ok = syndrome_ok();
-        if (p.early_stop && ok) break;
+        if (job.early_stop && ok) break;
       }
     }
-    for (int i = tid; i < p.n; i += blockDim.x) p.out_sym[(size_t)frame * p.n + i] = chat[i];
-    if (tid == 0) {
-      p.out_iters[frame] = iters;
-      p.out_ok[frame] = ok ? 1 : 0;
+    for (int i = stid; i < job.n; i += nthr) job.out_sym[(size_t)frame * job.n + i] = chat[i];
+    if (stid == 0) {
+      job.out_iters[frame] = iters;
+      job.out_ok[frame] = ok ? 1 : 0;
     }
-    __syncthreads();
+}
+
+// ---------------------------------------------------------------- the kernel
+// Persistent blocks of fpb frame slots; every slot takes work items (a frame
+// of one job) from a global counter until the list is exhausted.  QSEL = q,
+// VSEL = variant compiles the path of one field order and layout (single-code
+// launches); QSEL = 0, VSEL = -1 compiles every path (mixed-code launches).
+// Resident 256-thread blocks per SM the register allocation must allow: the
+// q >= 128 paths need more than 85 registers per thread without spilling.
+#ifndef NBLDPC_MINB_64
+#define NBLDPC_MINB_64 4
+#endif
+template <int QSEL> struct MinBlocks {
+  static constexpr int v = (QSEL == 0 || QSEL >= 128) ? 2 : (QSEL == 64 ? NBLDPC_MINB_64 : 4);
+};
+
+// VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
+template <int Q, int VSEL>
+__device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
+                                               uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
+  if constexpr (VSEL >= 0) {
+    decode_frame<Geo<Q, VSEL>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+  } else if (job.variant == 0) {
+    decode_frame<Geo<Q, 0>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+  } else {
+    decode_frame<Geo<Q, 1>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+  }
+}
+
+template <int QSEL, int VSEL>
+__global__ void __launch_bounds__(256, MinBlocks<QSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nthr = blockDim.x / p.fpb;
+  const int slot = threadIdx.x / nthr, stid = threadIdx.x % nthr;
+  const int bar_id = 1 + slot;
+  unsigned char* base = smem + (size_t)slot * p.slot_smem;
+  unsigned char* sblob = base;
+  uint8_t* chat = base + p.blob_cap;
+  volatile int* ctl = reinterpret_cast<volatile int*>(base + p.blob_cap + p.n_cap);
+  unsigned char* scratch = base + p.blob_cap + p.n_cap + 16;
+  uint8_t* X = p.msg + ((size_t)blockIdx.x * p.fpb + slot) * p.slot_bytes;
+  int staged = -1;
+
+  for (;;) {
+    if (stid == 0) ctl[0] = (int)atomicAdd(p.counter, 1u);
+    slot_sync(bar_id, nthr);
+    const int item = ctl[0];
+    if (item >= p.total_items) break;
+    int j = 0;
+    if constexpr (QSEL == 0)
+      while (j + 1 < p.njobs && item >= p.jobs[j + 1].item_begin) ++j;
+    // single-field launches carry one job: static parameter offsets
+    const JobDesc& job = (QSEL == 0) ? p.jobs[j] : p.jobs[0];
+    const int frame = item - job.item_begin;
+    if (j != staged) {      // stage the code description (GF tables, H, variable-node view)
+      for (int i = stid; i < job.off.bytes / 16; i += nthr)
+        reinterpret_cast<uint4*>(sblob)[i] = reinterpret_cast<const uint4*>(job.blob)[i];
+      staged = j;
+      slot_sync(bar_id, nthr);
+    }
+    if constexpr (QSEL != 0) {
+      decode_variant<QSEL, VSEL>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    } else {
+      switch (job.q) {
+        case 2: decode_variant<2, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 4: decode_variant<4, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 8: decode_variant<8, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 16: decode_variant<16, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 32: decode_variant<32, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 64: decode_variant<64, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 128: decode_variant<128, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        default: decode_variant<256, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+      }
+    }
+    slot_sync(bar_id, nthr);
   }
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the GB300 min-max NB-LDPC decoder (declarations and contracts in
 // include/nbldpc.h).  Host side: argument validation, GF tables, code upload,
-// launch configuration and stream-ordered launches of the decode kernel.
+// launch planning, the autotuner and stream-ordered launches of the decode
+// kernel.
 #include "nbldpc.h"
 
 #include <atomic>
@@ -16,12 +17,16 @@ namespace {
 
 std::atomic<uint64_t> g_launches{0};
 
-struct LaunchCfg {
-  int threads = 0;
-  int smem = 0;
-  int blocks_per_sm = 0;
-  int grid_max = 0;
-  int group_bytes = 0;
+// Launch shape of one kernel for one set of codes.
+struct Plan {
+  int fpb = 1;          // frame slots per block
+  int threads = 256;    // block size
+  int slot_smem = 0;    // shared bytes per frame slot
+  int smem = 0;         // shared bytes per block
+  int per_sm = 0;       // resident blocks per SM
+  int grid_max = 0;     // resident blocks on the device
+  int blob_cap = 0, n_cap = 0;
+  size_t slot_bytes = 0;  // message slot per frame slot
 };
 
 }  // namespace
@@ -32,7 +37,8 @@ struct nbldpc_code {
   int device = 0;
   unsigned char* blob_dev = nullptr;
   nbldpc::CodeBlob off{};
-  LaunchCfg cfg{};
+  int variant = 0;                     // layout variant used by every decode of this code
+  Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
   std::mutex mu;                       // guards the lazily created copy stream
   cudaStream_t side = nullptr;         // second stream for nbldpc_decode_host
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -40,7 +46,13 @@ struct nbldpc_code {
 
 namespace {
 
+constexpr int kThreads = 256;
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? NBLDPC_OK : NBLDPC_ERR_CUDA; }
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Field tables by repeated multiplication by x modulo the primitive
 // polynomial; fails unless x generates all q-1 non-zero elements.
@@ -65,37 +77,41 @@ bool build_field(int q, uint32_t poly, std::vector<uint8_t>& exp2, std::vector<u
   return true;
 }
 
-template <int Q> const void* kernel_ptr() { return reinterpret_cast<const void*>(&nbldpc::mma_decode_kernel<Q>); }
+template <int Q, int V> const void* kptr() { return reinterpret_cast<const void*>(&nbldpc::mma_decode_kernel<Q, V>); }
 
-const void* kernel_for(int q) {
+// kernel compiled for one field order and layout variant, or for all of them (q = 0)
+const void* kernel_for(int q, int v) {
   switch (q) {
-    case 2: return kernel_ptr<2>();
-    case 4: return kernel_ptr<4>();
-    case 8: return kernel_ptr<8>();
-    case 16: return kernel_ptr<16>();
-    case 32: return kernel_ptr<32>();
-    case 64: return kernel_ptr<64>();
-    case 128: return kernel_ptr<128>();
-    case 256: return kernel_ptr<256>();
+    case 0: return kptr<0, -1>();
+    case 2: return v ? kptr<2, 1>() : kptr<2, 0>();
+    case 4: return v ? kptr<4, 1>() : kptr<4, 0>();
+    case 8: return v ? kptr<8, 1>() : kptr<8, 0>();
+    case 16: return v ? kptr<16, 1>() : kptr<16, 0>();
+    case 32: return v ? kptr<32, 1>() : kptr<32, 0>();
+    case 64: return v ? kptr<64, 1>() : kptr<64, 0>();
+    case 128: return v ? kptr<128, 1>() : kptr<128, 0>();
+    case 256: return v ? kptr<256, 1>() : kptr<256, 0>();
   }
   return nullptr;
 }
 
-int group_lanes(int q) {
+template <int Q> int lanes(int v) { return v ? nbldpc::Geo<Q, 1>::G : nbldpc::Geo<Q, 0>::G; }
+
+int group_lanes(int q, int v) {
   switch (q) {
-    case 2: return nbldpc::Geo<2>::G;
-    case 4: return nbldpc::Geo<4>::G;
-    case 8: return nbldpc::Geo<8>::G;
-    case 16: return nbldpc::Geo<16>::G;
-    case 32: return nbldpc::Geo<32>::G;
-    case 64: return nbldpc::Geo<64>::G;
-    case 128: return nbldpc::Geo<128>::G;
-    case 256: return nbldpc::Geo<256>::G;
+    case 2: return lanes<2>(v);
+    case 4: return lanes<4>(v);
+    case 8: return lanes<8>(v);
+    case 16: return lanes<16>(v);
+    case 32: return lanes<32>(v);
+    case 64: return lanes<64>(v);
+    case 128: return lanes<128>(v);
+    case 256: return lanes<256>(v);
   }
   return 0;
 }
 
-int scratch_bytes(int q, int dmax) {
+int group_bytes(int q, int dmax) {
   switch (q) {
     case 2: return nbldpc::group_scratch_bytes<2>(dmax);
     case 4: return nbldpc::group_scratch_bytes<4>(dmax);
@@ -109,81 +125,154 @@ int scratch_bytes(int q, int dmax) {
   return 0;
 }
 
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+// Every kernel may use up to the opt-in shared memory of the device (set once
+// per device and kernel; occupancy still follows the bytes of each launch).
+std::mutex g_attr_mu;
+bool g_attr_done[64][17] = {};
 
-// Block size, shared memory and resident blocks for a code on the current device.
-int configure(nbldpc_code* c) {
-  int dev = 0, sms = 0, smem_optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  const int G = group_lanes(c->q);
-  const int work = (c->m > c->n ? c->m : c->n) * G;
-  int threads = (int)round_up((size_t)work, 32);
-  if (threads > 256) threads = 256;
-  if (threads < 32) threads = 32;
-  const int gb = scratch_bytes(c->q, c->dmax);
-  const int fixed = c->off.bytes + (int)round_up((size_t)c->n, 16) + 64;
-  while (threads > 32 && fixed + (threads / G) * gb > smem_optin) threads -= 32;
-  const int smem = fixed + (threads / G) * gb;
-  if (smem > smem_optin) return NBLDPC_ERR_UNSUPPORTED;
-  const void* k = kernel_for(c->q);
-  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  if (per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
-  c->cfg.threads = threads;
-  c->cfg.smem = smem;
-  c->cfg.blocks_per_sm = per_sm;
-  c->cfg.grid_max = per_sm * sms;
-  c->cfg.group_bytes = gb;
+int kernel_slot(int q, int v) { return q == 0 ? 0 : 2 * (nbldpc::ilog2(q) - 1) + 1 + (v ? 1 : 0); }
+
+int prepare_kernel(int q, int v, int dev, int smem_optin) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
+  bool& done = g_attr_done[dev][kernel_slot(q, v)];
+  if (!done) {
+    if (cudaFuncSetAttribute(kernel_for(q, v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
+      return NBLDPC_ERR_CUDA;
+    done = true;
+  }
   return NBLDPC_OK;
 }
 
-size_t slot_bytes(const nbldpc_code* c) { return round_up((size_t)c->nnz * c->q, 256); }
+struct CodeNeeds {       // what one code asks of a frame slot
+  int q, variant, dmax, blob, n;
+  size_t msg;
+};
 
-int grid_for(const nbldpc_code* c, int frames) { return frames < c->cfg.grid_max ? frames : c->cfg.grid_max; }
-
-size_t decode_ws_bytes(const nbldpc_code* c, int frames) {
-  return 256 + (size_t)grid_for(c, frames) * slot_bytes(c);
+CodeNeeds needs_of(const nbldpc_code* c, int variant) {
+  return CodeNeeds{c->q, variant, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q, 256)};
 }
 
-int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
-           uint8_t* sym, int32_t* iters, uint8_t* ok, void* ws, cudaStream_t st) {
-  if (frames == 0) return NBLDPC_OK;
-  nbldpc::DecodeParams prm{};
-  prm.gamma = gamma;
-  prm.out_sym = sym;
-  prm.out_iters = iters;
-  prm.out_ok = ok;
-  prm.counter = reinterpret_cast<unsigned int*>(ws);
-  prm.msg = reinterpret_cast<uint8_t*>(ws) + 256;
-  prm.blob = c->blob_dev;
-  prm.off = c->off;
-  prm.slot_bytes = slot_bytes(c);
-  prm.n = c->n;
-  prm.m = c->m;
-  prm.nnz = c->nnz;
-  prm.dmax = c->dmax;
-  prm.frames = frames;
-  prm.max_iters = max_iters;
-  prm.early_stop = early_stop ? 1 : 0;
-  prm.group_bytes = c->cfg.group_bytes;
-  prm.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned int), st);
+// Plan a launch of kernel (kq, kv) with fpb frame slots per block for a set of codes.
+int make_plan(int kq, int kv, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
+  if (fpb < 1 || kThreads % fpb) return NBLDPC_ERR_ARG;
+  const int nthr = kThreads / fpb;
+  if (nthr < 32) return NBLDPC_ERR_UNSUPPORTED;
+  Plan pl{};
+  pl.fpb = fpb;
+  pl.threads = kThreads;
+  int scratch = 0;
+  for (int i = 0; i < nc; ++i) {
+    const int G = group_lanes(cs[i].q, cs[i].variant);
+    if (G > nthr) return NBLDPC_ERR_UNSUPPORTED;
+    const int s = (nthr / G) * group_bytes(cs[i].q, cs[i].dmax);
+    if (s > scratch) scratch = s;
+    if (cs[i].blob > pl.blob_cap) pl.blob_cap = cs[i].blob;
+    if (cs[i].n > pl.n_cap) pl.n_cap = cs[i].n;
+    if (cs[i].msg > pl.slot_bytes) pl.slot_bytes = cs[i].msg;
+  }
+  pl.blob_cap = (int)round_up((size_t)pl.blob_cap, 16);
+  pl.n_cap = (int)round_up((size_t)pl.n_cap, 16);
+  pl.slot_smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16 + scratch), 16);
+  pl.smem = fpb * pl.slot_smem;
+  if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
+  int st = prepare_kernel(kq, kv, dev, optin);
+  if (st != NBLDPC_OK) return st;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv), pl.threads, pl.smem) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
+  if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
+  pl.grid_max = pl.per_sm * sms;
+  *out = pl;
+  return NBLDPC_OK;
+}
+
+// Frame slots per block when nothing better is known: enough threads per slot
+// for the checks and variable nodes of one frame, at least one warp.
+int default_fpb(const nbldpc_code* c) {
+  const int G = group_lanes(c->q, 0);
+  const int work = c->m * G;
+  int fpb = 1;
+  while (fpb < 8 && kThreads / (2 * fpb) >= 32 && kThreads / (2 * fpb) >= work && kThreads / (2 * fpb) >= G) fpb *= 2;
+  return fpb;
+}
+
+int configure(nbldpc_code* c, int variant, int fpb) {
+  Plan pl{};
+  const CodeNeeds need = needs_of(c, variant);
+  const int st = make_plan(c->q, variant, fpb, &need, 1, &pl);
+  if (st != NBLDPC_OK) return st;
+  c->variant = variant;
+  c->plan = pl;
+  return NBLDPC_OK;
+}
+
+int grid_for(const Plan& pl, int frames) {
+  const int want = (frames + pl.fpb - 1) / pl.fpb;
+  return want < pl.grid_max ? want : pl.grid_max;
+}
+
+size_t ws_bytes(const Plan& pl, int frames) { return 256 + (size_t)grid_for(pl, frames) * pl.fpb * pl.slot_bytes; }
+
+size_t decode_ws_bytes(const nbldpc_code* c, int frames) { return ws_bytes(c->plan, frames); }
+
+nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
+                         uint8_t* sym, int32_t* iters, uint8_t* ok, int item_begin) {
+  nbldpc::JobDesc j{};
+  j.blob = c->blob_dev;
+  j.off = c->off;
+  j.gamma = gamma;
+  j.out_sym = sym;
+  j.out_iters = iters;
+  j.out_ok = ok;
+  j.q = c->q;
+  j.n = c->n;
+  j.m = c->m;
+  j.dmax = c->dmax;
+  j.variant = c->variant;
+  j.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
+  j.group_bytes = group_bytes(c->q, c->dmax);
+  j.frames = frames;
+  j.max_iters = max_iters;
+  j.early_stop = early_stop ? 1 : 0;
+  j.item_begin = item_begin;
+  return j;
+}
+
+// Queue the counter reset and the persistent kernel (grid blocks) on st.
+int launch_plan(const void* kernel, const Plan& pl, nbldpc::LaunchParams& lp, int grid, void* counter, uint8_t* msg,
+                cudaStream_t st) {
+  if (lp.total_items == 0 || grid < 1) return NBLDPC_OK;
+  lp.counter = reinterpret_cast<unsigned int*>(counter);
+  lp.msg = msg;
+  lp.slot_bytes = pl.slot_bytes;
+  lp.fpb = pl.fpb;
+  lp.slot_smem = pl.slot_smem;
+  lp.blob_cap = pl.blob_cap;
+  lp.n_cap = pl.n_cap;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  const int grid = grid_for(c, frames);
-  void* args[] = {&prm};
-  e = cudaLaunchKernel(kernel_for(c->q), dim3(grid), dim3(c->cfg.threads), args, (size_t)c->cfg.smem, st);
+  void* args[] = {&lp};
+  e = cudaLaunchKernel(kernel, dim3(grid), dim3(pl.threads), args, (size_t)pl.smem, st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return NBLDPC_OK;
 }
 
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop, uint8_t* sym,
+           int32_t* iters, uint8_t* ok, void* ws, cudaStream_t st) {
+  if (frames == 0) return NBLDPC_OK;
+  nbldpc::LaunchParams lp{};
+  lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0);
+  lp.njobs = 1;
+  lp.total_items = frames;
+  return launch_plan(kernel_for(c->q, c->variant), c->plan, lp, grid_for(c->plan, frames), ws,
+                     reinterpret_cast<uint8_t*>(ws) + 256, st);
+}
 
 // ---- non-allocating decode (nbldpc_decode_noalloc) -------------------------
 // Fixed scratch for callers that cannot allocate: frame counter + message slots.
@@ -207,35 +296,8 @@ int noalloc_scratch(void** out) {
   return NBLDPC_OK;
 }
 
-int launch_noalloc(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
-                   uint8_t* sym, int32_t* iters, uint8_t* ok, void* scratch, int grid, cudaStream_t st) {
-  nbldpc::DecodeParams prm{};
-  prm.gamma = gamma;
-  prm.out_sym = sym;
-  prm.out_iters = iters;
-  prm.out_ok = ok;
-  prm.counter = reinterpret_cast<unsigned int*>(scratch);
-  prm.msg = reinterpret_cast<uint8_t*>(scratch) + 256;
-  prm.blob = c->blob_dev;
-  prm.off = c->off;
-  prm.slot_bytes = slot_bytes(c);
-  prm.n = c->n;
-  prm.m = c->m;
-  prm.nnz = c->nnz;
-  prm.dmax = c->dmax;
-  prm.frames = frames;
-  prm.max_iters = max_iters;
-  prm.early_stop = early_stop ? 1 : 0;
-  prm.group_bytes = c->cfg.group_bytes;
-  prm.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
-  // the array keeps the previous call's contents: the frame counter must start at zero
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  void* args[] = {&prm};
-  e = cudaLaunchKernel(kernel_for(c->q), dim3(grid), dim3(c->cfg.threads), args, (size_t)c->cfg.smem, st);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return NBLDPC_OK;
+bool valid_outputs(const uint8_t* gamma, const uint8_t* sym, const int32_t* iters, const uint8_t* ok) {
+  return gamma && sym && iters && ok && aligned(gamma, 16) && aligned(iters, 4);
 }
 
 }  // namespace
@@ -247,20 +309,25 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
                           void* cuda_stream) {
   if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
   if (frames == 0) return NBLDPC_OK;
-  if (!gamma_dev || !out_sym_dev || !out_iters_dev || !out_ok_dev) return NBLDPC_ERR_ARG;
-  if (!aligned(gamma_dev, 16) || !aligned(out_iters_dev, 4)) return NBLDPC_ERR_ARG;
-  const size_t slot = slot_bytes(c);
-  if (256 + slot > (size_t)NBLDPC_NOALLOC_SCRATCH_BYTES) return NBLDPC_ERR_UNSUPPORTED;
-  const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / slot);
-  int grid = grid_for(c, frames);
+  if (!valid_outputs(gamma_dev, out_sym_dev, out_iters_dev, out_ok_dev)) return NBLDPC_ERR_ARG;
+  const Plan& pl = c->plan;
+  const size_t per_block = (size_t)pl.fpb * pl.slot_bytes;
+  if (256 + per_block > (size_t)NBLDPC_NOALLOC_SCRATCH_BYTES) return NBLDPC_ERR_UNSUPPORTED;
+  const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / per_block);
+  int grid = grid_for(pl, frames);
   if (grid > fit) grid = fit;
   int st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   void* scratch = nullptr;
   st = noalloc_scratch(&scratch);
   if (st != NBLDPC_OK) return st;
-  return launch_noalloc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev,
-                        scratch, grid, reinterpret_cast<cudaStream_t>(cuda_stream));
+  // the array keeps the previous call's contents: the frame counter is cleared in launch_plan
+  nbldpc::LaunchParams lp{};
+  lp.jobs[0] = job_desc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, 0);
+  lp.njobs = 1;
+  lp.total_items = frames;
+  return launch_plan(kernel_for(c->q, c->variant), pl, lp, grid, scratch, reinterpret_cast<uint8_t*>(scratch) + 256,
+                     reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 const char* nbldpc_status_string(int status) {
@@ -365,7 +432,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   if (e != cudaSuccess) { delete c; return e == cudaErrorMemoryAllocation ? NBLDPC_ERR_NOMEM : NBLDPC_ERR_CUDA; }
   e = cudaMemcpy(c->blob_dev, blob.data(), o, cudaMemcpyHostToDevice);
   int st = cuda_status(e);
-  if (st == NBLDPC_OK) st = configure(c);
+  if (st == NBLDPC_OK) st = configure(c, 0, default_fpb(c));
   if (st != NBLDPC_OK) {
     cudaFree(c->blob_dev);
     delete c;
@@ -393,6 +460,20 @@ int nbldpc_code_info(const nbldpc_code* c, int* q, int* n, int* m, int* nnz) {
   return NBLDPC_OK;
 }
 
+int nbldpc_code_get_tuning(const nbldpc_code* c, int* variant, int* frames_per_block) {
+  if (!c) return NBLDPC_ERR_ARG;
+  if (variant) *variant = c->variant;
+  if (frames_per_block) *frames_per_block = c->plan.fpb;
+  return NBLDPC_OK;
+}
+
+int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
+  if (!c || variant < 0 || variant > 1 || frames_per_block < 1 || frames_per_block > 8 ||
+      (frames_per_block & (frames_per_block - 1)))
+    return NBLDPC_ERR_ARG;
+  return configure(c, variant, frames_per_block);
+}
+
 int nbldpc_decode_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
   if (!c || !bytes || frames < 0) return NBLDPC_ERR_ARG;
   *bytes = decode_ws_bytes(c, frames);
@@ -404,13 +485,134 @@ int nbldpc_decode(const nbldpc_code* c, const uint8_t* gamma_dev, int frames, in
                   size_t workspace_bytes, void* cuda_stream) {
   if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
   if (frames == 0) return NBLDPC_OK;
-  if (!gamma_dev || !out_sym_dev || !out_iters_dev || !out_ok_dev || !workspace_dev) return NBLDPC_ERR_ARG;
-  if (!aligned(gamma_dev, 16) || !aligned(workspace_dev, 16) || !aligned(out_iters_dev, 4)) return NBLDPC_ERR_ARG;
+  if (!valid_outputs(gamma_dev, out_sym_dev, out_iters_dev, out_ok_dev) || !workspace_dev) return NBLDPC_ERR_ARG;
+  if (!aligned(workspace_dev, 16)) return NBLDPC_ERR_ARG;
   if (workspace_bytes < decode_ws_bytes(c, frames)) return NBLDPC_ERR_ARG;
   int st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   return launch(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev,
                 workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+// ---- mixed-code batches -----------------------------------------------------
+static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) {
+  if (!jobs || n_jobs < 1 || n_jobs > NBLDPC_MAX_BATCH_JOBS) return NBLDPC_ERR_ARG;
+  CodeNeeds need[NBLDPC_MAX_BATCH_JOBS];
+  int fpb = 8;
+  long long t = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nbldpc_code* c = jobs[i].code;
+    if (!c || jobs[i].frames < 0 || jobs[i].max_iters < 0) return NBLDPC_ERR_ARG;
+    need[i] = needs_of(c, c->variant);
+    if (c->plan.fpb < fpb) fpb = c->plan.fpb;
+    t += jobs[i].frames;
+  }
+  if (t > 0x7FFFFFFF) return NBLDPC_ERR_ARG;
+  *total = (int)t;
+  return make_plan(0, -1, fpb, need, n_jobs, pl);
+}
+
+int nbldpc_decode_batch_workspace_size(const nbldpc_job* jobs, int n_jobs, size_t* bytes) {
+  if (!bytes) return NBLDPC_ERR_ARG;
+  Plan pl{};
+  int total = 0;
+  const int st = batch_plan(jobs, n_jobs, &pl, &total);
+  if (st != NBLDPC_OK) return st;
+  *bytes = ws_bytes(pl, total);
+  return NBLDPC_OK;
+}
+
+int nbldpc_decode_batch(const nbldpc_job* jobs, int n_jobs, void* workspace_dev, size_t workspace_bytes,
+                        void* cuda_stream) {
+  Plan pl{};
+  int total = 0;
+  int st = batch_plan(jobs, n_jobs, &pl, &total);
+  if (st != NBLDPC_OK) return st;
+  if (!workspace_dev || !aligned(workspace_dev, 16) || workspace_bytes < ws_bytes(pl, total)) return NBLDPC_ERR_ARG;
+  nbldpc::LaunchParams lp{};
+  int begin = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nbldpc_job& j = jobs[i];
+    if (j.frames > 0 && !valid_outputs(j.gamma_dev, j.out_sym_dev, j.out_iters_dev, j.out_ok_dev))
+      return NBLDPC_ERR_ARG;
+    lp.jobs[i] = job_desc(j.code, j.gamma_dev, j.frames, j.max_iters, j.early_stop, j.out_sym_dev, j.out_iters_dev,
+                          j.out_ok_dev, begin);
+    begin += j.frames;
+  }
+  lp.njobs = n_jobs;
+  lp.total_items = total;
+  st = cuda_status(cudaGetLastError());
+  if (st != NBLDPC_OK) return st;
+  return launch_plan(kernel_for(0, -1), pl, lp, grid_for(pl, total), workspace_dev,
+                     reinterpret_cast<uint8_t*>(workspace_dev) + 256, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+// ---- autotuner ----------------------------------------------------------------
+static size_t tune_outputs(const nbldpc_code* c, int frames) {
+  return round_up((size_t)frames * c->n, 256) + round_up((size_t)frames * 4, 256) + round_up((size_t)frames, 256);
+}
+
+int nbldpc_code_autotune_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
+  if (!c || !bytes || frames < 1) return NBLDPC_ERR_ARG;
+  size_t mx = 0;
+  for (int v = 0; v < 2; ++v)
+    for (int fpb = 1; fpb <= 8; fpb *= 2) {
+      Plan pl{};
+      const CodeNeeds need = needs_of(c, v);
+      if (make_plan(c->q, v, fpb, &need, 1, &pl) != NBLDPC_OK) continue;
+      const size_t w = ws_bytes(pl, frames);
+      if (w > mx) mx = w;
+    }
+  *bytes = tune_outputs(c, frames) + mx;
+  return NBLDPC_OK;
+}
+
+int nbldpc_code_autotune(nbldpc_code* c, const uint8_t* gamma_dev, int frames, int max_iters, void* workspace_dev,
+                         size_t workspace_bytes, void* cuda_stream, nbldpc_tune_result* results, int max_results,
+                         int* n_results) {
+  if (!c || !gamma_dev || frames < 1 || max_iters < 1 || !workspace_dev || !aligned(gamma_dev, 16) ||
+      !aligned(workspace_dev, 256))
+    return NBLDPC_ERR_ARG;
+  size_t need = 0;
+  int st = nbldpc_code_autotune_workspace_size(c, frames, &need);
+  if (st != NBLDPC_OK) return st;
+  if (workspace_bytes < need) return NBLDPC_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  unsigned char* w = reinterpret_cast<unsigned char*>(workspace_dev);
+  uint8_t* sym = w;
+  int32_t* its = reinterpret_cast<int32_t*>(w + round_up((size_t)frames * c->n, 256));
+  uint8_t* okb = w + round_up((size_t)frames * c->n, 256) + round_up((size_t)frames * 4, 256);
+  void* dws = w + tune_outputs(c, frames);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NBLDPC_ERR_CUDA;
+  const int v_old = c->variant, f_old = c->plan.fpb;
+  int best_v = v_old, best_f = f_old, count = 0;
+  float best = 3.4e38f;
+  st = NBLDPC_OK;
+  for (int v = 0; v < 2 && st == NBLDPC_OK; ++v)
+    for (int fpb = 1; fpb <= 8 && st == NBLDPC_OK; fpb *= 2) {
+      if (configure(c, v, fpb) != NBLDPC_OK) continue;
+      // one untimed decode, then one timed decode with fixed iterations
+      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s);
+      if (st != NBLDPC_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = NBLDPC_ERR_CUDA; break; }
+      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s);
+      if (st != NBLDPC_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = NBLDPC_ERR_CUDA;
+        break;
+      }
+      if (results && count < max_results) results[count] = nbldpc_tune_result{v, fpb, ms};
+      ++count;
+      if (ms < best) { best = ms; best_v = v; best_f = fpb; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int st2 = configure(c, st == NBLDPC_OK ? best_v : v_old, st == NBLDPC_OK ? best_f : f_old);
+  if (n_results) *n_results = count;
+  return st != NBLDPC_OK ? st : st2;
 }
 
 int nbldpc_decode_host_workspace_size(const nbldpc_code* c, int chunk_frames, size_t* bytes) {

@@ -232,3 +232,115 @@ def test_generator_is_device_independent():
     a = I.make_batch(code, 2.0, 99, 40, device="cpu")
     b = I.make_batch(code, 2.0, 99, 40, device="cuda")
     assert torch.equal(a.gamma, b.gamma.cpu()) and torch.equal(a.codewords, b.codewords.cpu())
+
+
+# --------------------------------------------------------------- layout variants and frames per block
+TUNE_CODES = [("gf4_n48_dv2_dc4", None), ("gf64_n576_dv2_dc4", None), ("gf32_n600_dv3_dc6", None),
+              ("gf256_n128_dv2_dc8", None), ("q2", (2, 60, 3, 6)), ("q8", (8, 64, 2, 4)),
+              ("q16", (16, 96, 2, 4)), ("q128", (128, 96, 2, 4))]
+
+
+@pytest.mark.parametrize("name,shape", TUNE_CODES)
+def test_every_variant_and_frames_per_block(name, shape):
+    if shape is None:
+        code = I.workload_code(name)
+        eb = 1.5
+    else:
+        q, n, dv, dc = shape
+        code = I.make_regular_code(q, n, dv, dc, seed=7 * q + n)
+        eb = 1.0
+    frames = 20
+    g = I.make_batch(code, eb, 404, frames).gamma.numpy()
+    want = oracle.decode(code, g, 8, 1, threads=THREADS)
+    dec = binding.Decoder.from_code(code)
+    gd = torch.as_tensor(g).cuda()
+    tried = 0
+    for v in (0, 1):
+        for fpb in (1, 2, 4, 8):
+            try:
+                dec.set_tuning(v, fpb)
+            except binding.NbldpcError as e:
+                assert e.status == binding.NBLDPC_ERR_UNSUPPORTED
+                continue
+            assert dec.tuning() == (v, fpb)
+            got = [t.cpu().numpy() for t in dec.decode(gd, 8, 1)]
+            assert_same(got, want, f"{name} variant {v} fpb {fpb}")
+            tried += 1
+    assert tried >= 2
+
+
+def test_autotune_picks_a_valid_pair_and_keeps_results():
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    g = I.make_batch(code, 2.0, 505, 64).gamma
+    dec = binding.Decoder.from_code(code)
+    res = dec.autotune(g.cuda(), 3)
+    assert len(res) >= 2 and all(ms > 0 for _, _, ms in res)
+    best = min(res, key=lambda r: r[2])
+    assert dec.tuning() == (best[0], best[1])
+    got = [t.cpu().numpy() for t in dec.decode(g.cuda(), 30, 1)]
+    assert_same(got, oracle.decode(code, g.numpy(), 30, 1, threads=THREADS), "after autotune")
+
+
+# --------------------------------------------------------------- mixed-code batches
+def _batch_jobs(specs):
+    jobs, keep = [], []
+    for code, g, mi, es in specs:
+        dec = binding.Decoder.from_code(code)
+        f = g.shape[0]
+        gd = torch.as_tensor(g).cuda().contiguous()
+        sym = torch.empty((f, code.n), dtype=torch.uint8, device="cuda")
+        its = torch.empty((f,), dtype=torch.int32, device="cuda")
+        ok = torch.empty((f,), dtype=torch.uint8, device="cuda")
+        keep.append((dec, gd, sym, its, ok))
+        jobs.append((dec.handle, gd, f, mi, es, sym, its, ok))
+    return jobs, keep
+
+
+def test_mixed_code_batch_matches_oracle():
+    specs = []
+    for name, frames, eb in (("gf16_n1024_dv2_dc4", 37, 1.5), ("gf64_n576_dv2_dc4", 5, 2.0),
+                             ("gf32_n600_dv3_dc6", 23, 2.5), ("gf256_n128_dv2_dc8", 11, 3.5),
+                             ("gf4_n48_dv2_dc4", 300, 3.0), ("gf256_n384_dv2_dc6", 0, 2.5)):
+        w = I.WORKLOADS[name]
+        code = I.workload_code(name)
+        g = I.make_batch(code, eb, 606, frames).gamma.numpy() if frames else \
+            np.zeros((0, code.n, code.q), np.uint8)
+        specs.append((code, g, w["max_iters"], w["early_stop"]))
+    jobs, keep = _batch_jobs(specs)
+    ws = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device="cuda")
+    before = binding.nbldpc_kernel_launch_count()
+    binding.nbldpc_decode_batch(jobs, ws)
+    torch.cuda.synchronize()
+    assert binding.nbldpc_kernel_launch_count() == before + 1
+    for (code, g, mi, es), (_, _, sym, its, ok) in zip(specs, keep):
+        if g.shape[0] == 0:
+            continue
+        want = oracle.decode(code, g, mi, es, threads=THREADS)
+        assert_same([sym.cpu().numpy(), its.cpu().numpy(), ok.cpu().numpy()], want, f"batch q={code.q}")
+
+
+def test_mixed_batch_replays_from_a_cuda_graph():
+    names = ("gf16_n1024_dv2_dc4", "gf256_n128_dv2_dc8")
+    specs = []
+    for name in names:
+        w = I.WORKLOADS[name]
+        code = I.workload_code(name)
+        specs.append((code, I.make_batch(code, 2.0, 707, 16).gamma.numpy(), w["max_iters"], w["early_stop"]))
+    jobs, keep = _batch_jobs(specs)
+    ws = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    binding.nbldpc_decode_batch(jobs, ws, stream=s)      # first call outside capture
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        binding.nbldpc_decode_batch(jobs, ws, stream=s)
+    for rnd in range(2):
+        # new inputs in the same buffers, then replay
+        for (code, _, mi, es), (dec, gd, sym, its, ok) in zip(specs, keep):
+            fresh = I.make_batch(code, 1.5 + rnd, 808 + rnd, 16).gamma
+            gd.copy_(fresh.cuda())
+        graph.replay()
+        torch.cuda.synchronize()
+        for (code, _, mi, es), (dec, gd, sym, its, ok) in zip(specs, keep):
+            want = oracle.decode(code, gd.cpu().numpy(), mi, es, threads=THREADS)
+            assert_same([sym.cpu().numpy(), its.cpu().numpy(), ok.cpu().numpy()], want, f"replay {rnd}")
