@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed"],
+                    help="gf64: the GF(64) N=576 headline step; mixed: the four-code batch, persistent vs plain")
     ap.add_argument("--frames", type=int, default=None, help="frames per Eb/N0 point (default: 65536)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -193,11 +195,122 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def pairs_per_frame_iter(code):
+    """Min-max pairs of one check-node pass: sum over checks of 3(d-2) q^2."""
+    d = np.diff(code.row_ptr).astype(np.int64)
+    return int((3 * np.maximum(d - 2, 0)).sum()) * code.q * code.q
+
+
+def run_mixed(args, ws, rank, local):
+    """Four codes in one persistent launch (graph-replayed) against one
+    fixed-iteration launch per code (the plain batch decoder)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding, inputs as I
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    counts = I.mixed_frame_counts()
+    codes = [I.workload_code(n) for n in I.MIXED_SET]
+    max_iters = 30
+    gam, cws, decs, outs, tuning = [], [], [], [], {}
+    for k, (code, f) in enumerate(zip(codes, counts)):
+        b = I.make_batch(code, I.MIXED_EBN0, I.MIXED_SEED * 100 + k + 7919 * rank, f, device=dev)
+        gam.append(b.gamma.contiguous())
+        cws.append(b.codewords)
+        d = binding.Decoder.from_code(code)
+        if not args.no_autotune:
+            d.autotune(gam[-1][: min(f, 2048)], 3)
+        tuning[code.name] = dict(zip(("variant", "frames_per_block"), d.tuning()))
+        decs.append(d)
+        outs.append((torch.empty((f, code.n), dtype=torch.uint8, device=dev),
+                     torch.empty((f,), dtype=torch.int32, device=dev),
+                     torch.empty((f,), dtype=torch.uint8, device=dev)))
+    jobs = [(d.handle, g, g.shape[0], max_iters, 1, *o) for d, g, o in zip(decs, gam, outs)]
+    wsb = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    info_bits = sum(f * c.k * c.p for c, f in zip(codes, counts))
+
+    def fer_of(sym_list):
+        bad = sum(int((s.to(torch.int64) != cw).any(1).sum()) for s, cw in zip(sym_list, cws))
+        return bad / sum(counts)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    # persistent mixed batch, captured once and replayed
+    for _ in range(args.warmup):
+        binding.nbldpc_decode_batch(jobs, wsb, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        binding.nbldpc_decode_batch(jobs, wsb, stream=stream)
+    def replay():
+        with torch.cuda.stream(stream):
+            graph.replay()
+    with ClockSampler(local) as clk:
+        t_pers = timed(replay, args.steps)
+    its_pers = [o[1].cpu().numpy().astype(np.int64) for o in outs]
+    fer_pers = fer_of([o[0] for o in outs])
+    pairs = sum(int(it.sum()) * pairs_per_frame_iter(c) for it, c in zip(its_pers, codes))
+
+    # plain: one fixed-iteration launch per code
+    def plain(early):
+        for d, g, (sym, its, ok) in zip(decs, gam, outs):
+            binding.nbldpc_decode(d.handle, g, g.shape[0], max_iters, early, sym, its, ok,
+                                  d.workspace(g.shape[0], dev), stream=stream)
+    for _ in range(args.warmup):
+        plain(0)
+    t_fixed = timed(lambda: plain(0), args.steps)
+    fer_fixed = fer_of([o[0] for o in outs])
+    for _ in range(2):
+        plain(1)
+    t_early = timed(lambda: plain(1), args.steps)
+    mhz, mhz_kind = sm_max_mhz()
+    peak = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
+    achieved = 2 * pairs / (t_pers / args.steps) / 1e9
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "decoded info Mbit/s", "value": ws * args.steps * info_bits / t_pers / 1e6, "unit": "Mbit/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_pers / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "mixed4: GF(16) N=1024 (2,4) + GF(64) N=576 (2,4) + GF(32) N=600 (3,6) "
+                               "+ GF(256) N=128 (2,8)", "frames": dict(zip(I.MIXED_SET, counts)),
+                   "ebn0_db": "uniform per frame in [1.5, 3.5)", "max_iters": max_iters,
+                   "form": "one persistent launch per step (CUDA graph replay), early stop + refill",
+                   "tuning": tuning},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                     "frac": achieved / peak, "traffic": None},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,   # one decode kernel per graph replay
+        "fer": fer_pers,
+        "plain_fixed_iterations": {"value": ws * args.steps * info_bits / t_fixed / 1e6, "unit": "Mbit/s",
+                                   "ms_per_step": 1e3 * t_fixed / args.steps, "fer": fer_fixed,
+                                   "form": "one launch per code, 30 iterations, no early stop"},
+        "plain_early_stop": {"value": ws * args.steps * info_bits / t_early / 1e6, "unit": "Mbit/s",
+                             "ms_per_step": 1e3 * t_early / args.steps,
+                             "form": "one launch per code, early stop"},
+        "mean_iters": {c.name: float(it.mean()) for c, it in zip(codes, its_pers)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "mixed":
+        return run_mixed(args, ws, rank, local)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     import __graft_entry__

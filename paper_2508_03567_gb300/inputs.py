@@ -289,12 +289,19 @@ def awgn(code: Code, seed: int, frame0: int, frames: int) -> torch.Tensor:
 
 
 def quantized_reliabilities(code: Code, codewords: torch.Tensor, noise: torch.Tensor,
-                            ebn0_db: float) -> torch.Tensor:
-    """gamma [F, N, q] uint8 from codewords [F, N] and unit noise [F, N, p]."""
+                            ebn0_db) -> torch.Tensor:
+    """gamma [F, N, q] uint8 from codewords [F, N] and unit noise [F, N, p].
+
+    ebn0_db is one value for every frame or a float64 tensor [F] of per-frame values."""
     dev = codewords.device
     q, p = code.q, code.p
-    s2 = sigma2_for(code, ebn0_db)
-    sigma = math.sqrt(s2)
+    if isinstance(ebn0_db, torch.Tensor):
+        rate = code.k / code.n
+        s2 = (1.0 / (2.0 * rate * torch.pow(10.0, ebn0_db.to(torch.float64) / 10.0))).to(dev)[:, None, None]
+        sigma = torch.sqrt(s2)
+    else:
+        s2 = sigma2_for(code, ebn0_db)
+        sigma = math.sqrt(s2)
     b = _bits(codewords, p).to(torch.float64)
     s = 1.0 - 2.0 * b
     y = s + sigma * noise.to(dev)
@@ -311,16 +318,27 @@ def quantized_reliabilities(code: Code, codewords: torch.Tensor, noise: torch.Te
     return torch.clamp(torch.round(4.0 * g), max=63.0).to(torch.uint8)
 
 
+def frame_ebn0(seed: int, frame0: int, frames: int, lo: float, hi: float) -> torch.Tensor:
+    """Per-frame Eb/N0 in dB, uniform in [lo, hi), block-seeded like the noise."""
+    out = []
+    for b, a, z in _blocks(frame0, frames):
+        rng = _block_rng(seed, b)
+        out.append(lo + (hi - lo) * rng.random(NOISE_BLOCK)[a:z])
+    return torch.from_numpy(np.concatenate(out) if out else np.zeros(0))
+
+
 @dataclass
 class Batch:
     gamma: torch.Tensor       # [F, N, q] uint8
     codewords: torch.Tensor   # [F, N] int64
 
 
-def make_batch(code: Code, ebn0_db: float, seed: int, frames: int, frame0: int = 0,
+def make_batch(code: Code, ebn0_db, seed: int, frames: int, frame0: int = 0,
                device: str | torch.device = "cpu", noiseless: bool = False,
                chunk: int = 4096) -> Batch:
-    """Frames [frame0, frame0+frames) of one (code, Eb/N0, seed) stream."""
+    """Frames [frame0, frame0+frames) of one (code, Eb/N0, seed) stream.
+
+    ebn0_db: one value, or a (lo, hi) pair for per-frame Eb/N0 uniform in [lo, hi)."""
     gam, cws = [], []
     for lo in range(0, frames, chunk):
         nf = min(chunk, frames - lo)
@@ -330,7 +348,8 @@ def make_batch(code: Code, ebn0_db: float, seed: int, frames: int, frame0: int =
             nz = torch.zeros(cw.shape + (code.p,), dtype=torch.float64)
         else:
             nz = awgn(code, seed + 1, frame0 + lo, nf)
-        gam.append(quantized_reliabilities(code, cw, nz, ebn0_db))
+        eb = frame_ebn0(seed + 2, frame0 + lo, nf, *ebn0_db) if isinstance(ebn0_db, tuple) else ebn0_db
+        gam.append(quantized_reliabilities(code, cw, nz, eb))
         cws.append(cw)
     if not gam:
         return Batch(torch.zeros((0, code.n, code.q), dtype=torch.uint8, device=device),
@@ -360,6 +379,20 @@ WORKLOADS = {
     "gf256_n128_dv2_dc8": dict(q=256, n=128, dv=2, dc=8, code_seed=4104, data_seed=4204,
                                frames=4096, ebn0=(1.5, 3.5), max_iters=30, early_stop=1),
 }
+
+# The mixed-code set decoded together: frame counts per code from a seeded
+# lognormal with mean 4096 (sigma_ln = 1, mu = ln 4096 - 1/2, rounded, >= 1),
+# per-frame Eb/N0 uniform in [1.5, 3.5) dB, up to 30 iterations.
+MIXED_SET = ("gf16_n1024_dv2_dc4", "gf64_n576_dv2_dc4", "gf32_n600_dv3_dc6", "gf256_n128_dv2_dc8")
+MIXED_EBN0 = (1.5, 3.5)
+MIXED_SEED = 5151
+
+
+def mixed_frame_counts(seed: int = MIXED_SEED) -> list[int]:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mu = math.log(4096.0) - 0.5
+    return [max(1, int(round(v))) for v in rng.lognormal(mu, 1.0, size=len(MIXED_SET))]
+
 
 _CODE_CACHE: dict[str, Code] = {}
 
