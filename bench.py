@@ -56,8 +56,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed"],
-                    help="gf64: the GF(64) N=576 headline step; mixed: the four-code batch, persistent vs plain")
+    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed", "serving"],
+                    help="gf64: the GF(64) N=576 headline step; mixed: the four-code batch, persistent vs "
+                         "plain; serving: Poisson request arrivals, continuous batching vs plain")
+    ap.add_argument("--seconds", type=float, default=6.0, help="serving: arrival window per load point")
     ap.add_argument("--frames", type=int, default=None, help="frames per Eb/N0 point (default: 65536)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -304,6 +306,99 @@ def run_mixed(args, ws, rank, local):
     return 0
 
 
+def run_serving(args, ws, rank, local):
+    """Poisson arrivals of requests (one of the four mixed-set codes, uniform;
+    1-256 frames, uniform; per-frame Eb/N0 uniform in [1.5, 3.5) dB) served by
+    continuous batching, load swept over fractions of the measured peak, and
+    by the plain one-launch-per-request decoder."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding, inputs as I
+    from paper_2508_03567_gb300.serving import CudaExecutor, Request, Server, percentile
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    codes = [I.workload_code(n) for n in I.MIXED_SET]
+    decs = [binding.Decoder.from_code(c) for c in codes]
+    max_iters = 30
+    rng = np.random.Generator(np.random.PCG64(4242))
+    pool = []
+    for i in range(96):
+        k = int(rng.integers(len(codes)))
+        f = int(rng.integers(1, 257))
+        g = I.make_batch(codes[k], I.MIXED_EBN0, 60000 + i, f, device=dev).gamma.cpu().pin_memory()
+        pool.append((k, g))
+    if not args.no_autotune:
+        for k, d in enumerate(decs):
+            g = torch.cat([gg for kk, gg in pool if kk == k][:8]).to(dev)
+            d.autotune(g[:2048], 3)
+    bits_of = lambda k, f: f * codes[k].k * codes[k].p
+    mean_bits = float(np.mean([bits_of(k, g.shape[0]) for k, g in pool]))
+    budget = 8 << 30
+
+    def serve(mode, rate, seconds, seed, saturate=False, cap=60.0):
+        ex = CudaExecutor(decs, max_iters=max_iters, streams=3)
+        srv = Server(ex, budget_bytes=budget, streams=3, mode=mode)
+        r = np.random.Generator(np.random.PCG64(seed))
+        reqs = []
+        t0 = time.perf_counter()
+        if saturate:
+            for i in range(2 * len(pool)):
+                k, g = pool[i % len(pool)]
+                reqs.append(Request(rid=i, code=k, gamma=g))
+                srv.submit(reqs[-1], now=t0)
+        else:
+            t_next = t0 + r.exponential(1.0 / rate)
+            while True:
+                now = time.perf_counter()
+                while t_next <= now and t_next - t0 < seconds:
+                    k, g = pool[int(r.integers(len(pool)))]
+                    reqs.append(Request(rid=len(reqs), code=k, gamma=g))
+                    srv.submit(reqs[-1], now=t_next)
+                    t_next += r.exponential(1.0 / rate)
+                srv.poll()
+                if now - t0 >= seconds:
+                    break
+        while not srv.idle() and time.perf_counter() - t0 < seconds + cap:
+            srv.poll()
+        done = [q for q in reqs if q.t_done >= 0]
+        t_end = max(q.t_done for q in done)
+        bits = sum(bits_of(q.code, q.frames) for q in done)
+        lat = [1e3 * q.latency for q in done]
+        return {"offered_mbps": None if saturate else rate * mean_bits / 1e6,
+                "achieved_mbps": bits / (t_end - t0) / 1e6, "requests": len(reqs), "completed": len(done),
+                "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "launches": srv.launches,
+                "peak_resident_bytes": srv.peak_used}
+
+    serve("continuous", 0, 0, 1, saturate=True)      # warm-up
+    peak = serve("continuous", 0, 0, 2, saturate=True)
+    peak_plain = serve("plain", 0, 0, 3, saturate=True)
+    peak_bps = peak["achieved_mbps"] * 1e6
+    loads = []
+    for i, load in enumerate((0.10, 0.25, 0.50, 0.75, 0.90, 1.00)):
+        res = serve("continuous", load * peak_bps / mean_bits, args.seconds, 5000 + i)
+        res["load"] = load
+        loads.append(res)
+    plain = []
+    for i, load in enumerate((0.10, 0.25, 0.50)):
+        res = serve("plain", load * peak_bps / mean_bits, args.seconds, 5100 + i, cap=20.0)
+        res["load"] = load
+        plain.append(res)
+    line = {"metric": "decoded info Mbit/s; p50/p99 request latency", "value": peak["achieved_mbps"],
+            "unit": "Mbit/s", "n_gpus": 1, "steps": len(loads), "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serving: Poisson requests, code uniform over the four-code set, 1-256 "
+                                   "frames, Eb/N0 uniform per frame in [1.5, 3.5) dB, up to 30 iterations, "
+                                   "early stop, 8 GB resident budget",
+                       "streams": 3, "max_requests_per_launch": 32},
+            "peak_continuous": peak, "peak_plain": peak_plain, "loads_continuous": loads,
+            "loads_plain": plain}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -311,6 +406,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "mixed":
         return run_mixed(args, ws, rank, local)
+    if args.workload == "serving":
+        return run_serving(args, ws, rank, local)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     import __graft_entry__

@@ -152,7 +152,7 @@ int nbldpc_decode_host(const nbldpc_code *code, const uint8_t *gamma_host, int f
  * form of the paper's multicodeword mapping (Sec. 4: one frame per processing
  * unit, no synchronization between frames), extended to mixed codes.
  */
-#define NBLDPC_MAX_BATCH_JOBS 8
+#define NBLDPC_MAX_BATCH_JOBS 32
 
 typedef struct nbldpc_job {
   const nbldpc_code *code;  /* all codes of a batch on the same device */

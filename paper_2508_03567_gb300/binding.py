@@ -33,7 +33,7 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_code_autotune", "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
-NBLDPC_MAX_BATCH_JOBS = 8
+NBLDPC_MAX_BATCH_JOBS = 32
 
 
 class nbldpc_job(ctypes.Structure):

@@ -212,7 +212,7 @@ struct JobDesc {
   int item_begin;             // index of this job's first frame in the launch's work list
 };
 
-constexpr int kMaxJobs = 8;
+constexpr int kMaxJobs = 32;
 
 // One launch: up to kMaxJobs jobs whose frames form one work list, served by
 // persistent blocks of `fpb` frame slots each.

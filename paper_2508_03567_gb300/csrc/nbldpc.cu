@@ -13,6 +13,9 @@
 
 #include "mma_kernels.cuh"
 
+static_assert(nbldpc::kMaxJobs == NBLDPC_MAX_BATCH_JOBS, "job table size");
+static_assert(sizeof(nbldpc::LaunchParams) < 32000, "kernel parameter space");
+
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
