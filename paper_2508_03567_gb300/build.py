@@ -1,16 +1,23 @@
-"""Compile the CUDA decoder library (libnbldpc.so) in-tree for sm_103a."""
+"""Compile the CUDA decoder library (libnbldpc.so) in-tree for sm_103a.
+
+The kernel translation units (one per field order, plus the one serving every
+field order) compile in parallel; the host unit holds the C ABI.
+"""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libnbldpc.so")
-SOURCES = [os.path.join(HERE, "csrc", "nbldpc.cu")]
+OBJ_DIR = os.path.join(HERE, "_build")
+CSRC = os.path.join(HERE, "csrc")
+KERNEL_UNITS = (0, 2, 4, 8, 16, 32, 64, 128, 256)
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 
 
 def _nvcc() -> str:
@@ -23,18 +30,41 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = glob.glob(os.path.join(HERE, "csrc", "*")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    deps = glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(ROOT, "include", "*.h")) + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    if force or _stale():
-        tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [_nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), *SOURCES, "-o", tmp]
+def _units():
+    units = [(os.path.join(CSRC, "kernels.cu"), f"kernels_q{q}.o", [f"-DNBLDPC_KQ={q}"]) for q in KERNEL_UNITS]
+    units.append((os.path.join(CSRC, "nbldpc.cu"), "nbldpc.o", []))
+    return units
+
+
+def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+    if not (force or _stale()):
+        return LIB
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    nvcc = _nvcc()
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    pid = os.getpid()
+
+    def compile_unit(u):
+        src, obj, defs = u
+        out = os.path.join(OBJ_DIR, f"{pid}_{obj}")
+        cmd = [nvcc, *NVCC_FLAGS, *inc, *defs, "-c", src, "-o", out]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+        return out
+
+    units = _units()
+    with ThreadPoolExecutor(max_workers=jobs or min(len(units), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_unit, units))
+    tmp = LIB + f".{pid}.tmp"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp])
+    os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

@@ -1,0 +1,27 @@
+// One translation unit per kernel family, so the field orders compile in
+// parallel: built with -DNBLDPC_KQ=q for the two layout variants of field
+// order q (single-code launches), or -DNBLDPC_KQ=0 for the kernel that
+// serves every field order (mixed-code launches).
+#include "mma_kernels.cuh"
+
+#ifndef NBLDPC_KQ
+#error "NBLDPC_KQ must name the field order (or 0)"
+#endif
+
+#define NBLDPC_CAT2(a, b) a##b
+#define NBLDPC_CAT(a, b) NBLDPC_CAT2(a, b)
+
+namespace nbldpc {
+
+// Address of the decode kernel for layout variant v of this unit's field order.
+const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v) {
+#if NBLDPC_KQ == 0
+  (void)v;
+  return reinterpret_cast<const void*>(&mma_decode_kernel<0, -1>);
+#else
+  return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1>)
+           : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0>);
+#endif
+}
+
+}  // namespace nbldpc

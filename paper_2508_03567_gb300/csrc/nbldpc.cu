@@ -80,20 +80,34 @@ bool build_field(int q, uint32_t poly, std::vector<uint8_t>& exp2, std::vector<u
   return true;
 }
 
-template <int Q, int V> const void* kptr() { return reinterpret_cast<const void*>(&nbldpc::mma_decode_kernel<Q, V>); }
+}  // namespace
+
+namespace nbldpc {   // defined in kernels.cu, one translation unit per field order
+const void* kernel_q0(int v);
+const void* kernel_q2(int v);
+const void* kernel_q4(int v);
+const void* kernel_q8(int v);
+const void* kernel_q16(int v);
+const void* kernel_q32(int v);
+const void* kernel_q64(int v);
+const void* kernel_q128(int v);
+const void* kernel_q256(int v);
+}  // namespace nbldpc
+
+namespace {
 
 // kernel compiled for one field order and layout variant, or for all of them (q = 0)
 const void* kernel_for(int q, int v) {
   switch (q) {
-    case 0: return kptr<0, -1>();
-    case 2: return v ? kptr<2, 1>() : kptr<2, 0>();
-    case 4: return v ? kptr<4, 1>() : kptr<4, 0>();
-    case 8: return v ? kptr<8, 1>() : kptr<8, 0>();
-    case 16: return v ? kptr<16, 1>() : kptr<16, 0>();
-    case 32: return v ? kptr<32, 1>() : kptr<32, 0>();
-    case 64: return v ? kptr<64, 1>() : kptr<64, 0>();
-    case 128: return v ? kptr<128, 1>() : kptr<128, 0>();
-    case 256: return v ? kptr<256, 1>() : kptr<256, 0>();
+    case 0: return nbldpc::kernel_q0(-1);
+    case 2: return nbldpc::kernel_q2(v);
+    case 4: return nbldpc::kernel_q4(v);
+    case 8: return nbldpc::kernel_q8(v);
+    case 16: return nbldpc::kernel_q16(v);
+    case 32: return nbldpc::kernel_q32(v);
+    case 64: return nbldpc::kernel_q64(v);
+    case 128: return nbldpc::kernel_q128(v);
+    case 256: return nbldpc::kernel_q256(v);
   }
   return nullptr;
 }
