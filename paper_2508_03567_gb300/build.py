@@ -40,9 +40,12 @@ def _units():
     return units
 
 
-def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not (force or _stale()):
-        return LIB
+def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None,
+                  extra_flags=(), lib_path: str | None = None) -> str:
+    """Build libnbldpc.so (or lib_path, with extra nvcc flags such as -D tuning macros)."""
+    lib = lib_path or LIB
+    if not (force or extra_flags or lib_path or _stale()):
+        return lib
     os.makedirs(OBJ_DIR, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -50,8 +53,8 @@ def build_library(force: bool = False, verbose: bool = False, jobs: int | None =
 
     def compile_unit(u):
         src, obj, defs = u
-        out = os.path.join(OBJ_DIR, f"{pid}_{obj}")
-        cmd = [nvcc, *NVCC_FLAGS, *inc, *defs, "-c", src, "-o", out]
+        out = os.path.join(OBJ_DIR, f"{pid}_{abs(hash(tuple(extra_flags)))}_{obj}")
+        cmd = [nvcc, *NVCC_FLAGS, *inc, *defs, *extra_flags, "-c", src, "-o", out]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
@@ -60,12 +63,12 @@ def build_library(force: bool = False, verbose: bool = False, jobs: int | None =
     units = _units()
     with ThreadPoolExecutor(max_workers=jobs or min(len(units), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_unit, units))
-    tmp = LIB + f".{pid}.tmp"
+    tmp = lib + f".{pid}.tmp"
     subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp])
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

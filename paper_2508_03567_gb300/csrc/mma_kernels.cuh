@@ -64,7 +64,7 @@ template <> struct Layout<16, 1>  { static constexpr int LB = 3, SB = 0; };
 template <> struct Layout<32, 0>  { static constexpr int LB = 2, SB = 2; };
 template <> struct Layout<32, 1>  { static constexpr int LB = 3, SB = 1; };
 template <> struct Layout<64, 0>  { static constexpr int LB = 3, SB = 2; };
-template <> struct Layout<64, 1>  { static constexpr int LB = 4, SB = 1; };
+template <> struct Layout<64, 1>  { static constexpr int LB = 3, SB = 1; };
 template <> struct Layout<128, 0> { static constexpr int LB = 4, SB = 1; };
 template <> struct Layout<128, 1> { static constexpr int LB = 5, SB = 0; };
 template <> struct Layout<256, 0> { static constexpr int LB = 5, SB = 0; };
@@ -99,11 +99,15 @@ template <int Q_, int V_> struct Geo {
   static_assert(BPL == 1 || BPL == 2 || BPL == 4 || BPL == 8, "byte lanes");
 };
 
-// Of the XN * AWN maxima of one shuffle step, how many use vmax2_fma.
-#ifndef NBLDPC_FMAMAX_64
-#define NBLDPC_FMAMAX_64 6
+// Of the XN * AWN maxima of one shuffle step, FmaEighths eighths use
+// vmax2_fma (the rest the ALU pipe, which also takes every minimum).  Measured
+// on GB300: 3/8 is best for q <= 64; for q >= 128 the ALU pipe is not the
+// limit and the extra issue slots of the FMA form cost throughput.
+#ifndef NBLDPC_FMA_EIGHTHS
+#define NBLDPC_FMA_EIGHTHS 3
 #endif
-template <int Q> struct FmaMax { static constexpr int v = Q == 64 ? NBLDPC_FMAMAX_64 : 0; };
+template <int Q> struct FmaEighths { static constexpr int v = Q >= 128 ? 0 : NBLDPC_FMA_EIGHTHS; };
+template <class g> struct FmaMax { static constexpr int v = (g::XN * g::AWN * FmaEighths<g::Q>::v) / 8; };
 
 // Lane constants of the convolution, computed once per thread.
 struct ConvLane {
@@ -173,7 +177,7 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
       for (int r = 0; r < g::XN; ++r)
 #pragma unroll
         for (int t = 0; t < g::AWN; ++t) {
-          const uint32_t m = (r * g::AWN + t < FmaMax<g::Q>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
+          const uint32_t m = (r * g::AWN + t < FmaMax<g>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
                                                               : vmax2(a[t], bl[dd][r ^ t]);
           acc[r] = (d == 0 && t == 0) ? m : vmin2(acc[r], m);
         }
@@ -547,8 +551,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 #ifndef NBLDPC_MINB_64
 #define NBLDPC_MINB_64 4
 #endif
-template <int QSEL> struct MinBlocks {
-  static constexpr int v = (QSEL == 0 || QSEL >= 128) ? 2 : (QSEL == 64 ? NBLDPC_MINB_64 : 4);
+template <int QSEL, int VSEL> struct MinBlocks {
+  static constexpr int v = (QSEL == 0 || QSEL >= 128) ? 2 : (QSEL == 64 ? (VSEL == 1 ? 3 : NBLDPC_MINB_64) : 4);
 };
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
@@ -565,7 +569,7 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
 }
 
 template <int QSEL, int VSEL>
-__global__ void __launch_bounds__(256, MinBlocks<QSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
   const int slot = threadIdx.x / nthr, stid = threadIdx.x % nthr;
