@@ -47,6 +47,21 @@ __device__ __forceinline__ uint32_t vmax2_fma(uint32_t a, uint32_t b) {
 }
 
 // ---------------------------------------------------------------- geometry
+// Bytes of one variable node's q-byte rows that each lane of the variable-node
+// pass handles (q / VBPL lanes per node).  Wide lanes put several nodes in
+// flight per warp and shorten the shuffle reductions; measured on GB300 the
+// 4-byte lanes of GF(64) left that pass latency-bound (8 bytes: +10 %).
+#ifndef NBLDPC_VBPL_64
+#define NBLDPC_VBPL_64 8
+#endif
+#ifndef NBLDPC_VBPL_256
+#define NBLDPC_VBPL_256 16
+#endif
+template <int Q> struct VnpBytes {
+  static constexpr int v = Q == 2 ? 2 : Q == 4 ? 4 : Q == 8 ? 8 : Q == 64 ? NBLDPC_VBPL_64
+                         : Q == 256 ? NBLDPC_VBPL_256 : 8;
+};
+
 // LB: lane bits of x (the shuffle offset d runs over them); SB: lane bits that
 // split the register part of y between lanes.  XB = p - LB register bits of x
 // per lane, TB = XB - SB register bits of y per lane.  Each field order has
@@ -90,7 +105,7 @@ template <int Q_, int V_> struct Geo {
   static constexpr int BPL = Q / G;             // bytes per lane when a group writes q bytes
   static constexpr int VB = (2 * Q + 15) / 16 * 16;  // bytes per 16-bit vector in smem
   // variable-node pass: VG lanes per variable node, VBPL bytes (VBPL/2 packed words) each
-  static constexpr int VBPL = Q >= 256 ? 8 : (Q >= 4 ? 4 : 2);
+  static constexpr int VBPL = VnpBytes<Q>::v;
   static constexpr int VG = Q / VBPL;
   static constexpr int VW = VBPL / 2;
   static_assert(LB >= 1 && TB >= 0 && XB == SB + TB, "layout");
@@ -274,10 +289,16 @@ template <int NB> __device__ __forceinline__ void load_pairs(const uint8_t* p, u
   } else if constexpr (NB == 4) {
     const uint32_t x = *reinterpret_cast<const uint32_t*>(p);
     w[0] = __byte_perm(x, 0, 0x4140); w[1] = __byte_perm(x, 0, 0x4342);
-  } else {
+  } else if constexpr (NB == 8) {
     const uint2 x = *reinterpret_cast<const uint2*>(p);
     w[0] = __byte_perm(x.x, 0, 0x4140); w[1] = __byte_perm(x.x, 0, 0x4342);
     w[2] = __byte_perm(x.y, 0, 0x4140); w[3] = __byte_perm(x.y, 0, 0x4342);
+  } else {
+    const uint4 x = *reinterpret_cast<const uint4*>(p);
+    w[0] = __byte_perm(x.x, 0, 0x4140); w[1] = __byte_perm(x.x, 0, 0x4342);
+    w[2] = __byte_perm(x.y, 0, 0x4140); w[3] = __byte_perm(x.y, 0, 0x4342);
+    w[4] = __byte_perm(x.z, 0, 0x4140); w[5] = __byte_perm(x.z, 0, 0x4342);
+    w[6] = __byte_perm(x.w, 0, 0x4140); w[7] = __byte_perm(x.w, 0, 0x4342);
   }
 }
 
@@ -287,11 +308,18 @@ template <int NB> __device__ __forceinline__ void store_pairs(uint8_t* p, const 
     *reinterpret_cast<uint16_t*>(p) = (uint16_t)__byte_perm(w[0], 0, 0x4420);
   } else if constexpr (NB == 4) {
     *reinterpret_cast<uint32_t*>(p) = __byte_perm(w[0], w[1], 0x6420);
-  } else {
+  } else if constexpr (NB == 8) {
     uint2 x;
     x.x = __byte_perm(w[0], w[1], 0x6420);
     x.y = __byte_perm(w[2], w[3], 0x6420);
     *reinterpret_cast<uint2*>(p) = x;
+  } else {
+    uint4 x;
+    x.x = __byte_perm(w[0], w[1], 0x6420);
+    x.y = __byte_perm(w[2], w[3], 0x6420);
+    x.z = __byte_perm(w[4], w[5], 0x6420);
+    x.w = __byte_perm(w[6], w[7], 0x6420);
+    *reinterpret_cast<uint4*>(p) = x;
   }
 }
 
