@@ -184,7 +184,7 @@ int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev,
  * 1: how the q x q min-max work of one convolution is split between the lanes
  * of a group and their registers) and the frames decoded side by side in one
  * 256-thread block (1, 2, 4 or 8; small codes leave threads idle at 1).
- * nbldpc_code_create picks variant 0 and a frames-per-block value from the
+ * nbldpc_code_create picks a default variant per field order and a frames-per-block value from the
  * code size; nbldpc_code_autotune measures every valid pair on the caller's
  * frames and keeps the fastest.
  */

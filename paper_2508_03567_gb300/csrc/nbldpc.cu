@@ -208,10 +208,14 @@ int make_plan(int kq, int kv, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   return NBLDPC_OK;
 }
 
+// Layout variant when nothing better is known: the one the autotuner picked for
+// the benchmark codes on GB300 (GF(16), GF(32), GF(64): variant 1).
+int default_variant(int q) { return (q >= 16 && q <= 64) ? 1 : 0; }
+
 // Frame slots per block when nothing better is known: enough threads per slot
 // for the checks and variable nodes of one frame, at least one warp.
 int default_fpb(const nbldpc_code* c) {
-  const int G = group_lanes(c->q, 0);
+  const int G = group_lanes(c->q, default_variant(c->q));
   const int work = c->m * G;
   int fpb = 1;
   while (fpb < 8 && kThreads / (2 * fpb) >= 32 && kThreads / (2 * fpb) >= work && kThreads / (2 * fpb) >= G) fpb *= 2;
@@ -449,7 +453,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   if (e != cudaSuccess) { delete c; return e == cudaErrorMemoryAllocation ? NBLDPC_ERR_NOMEM : NBLDPC_ERR_CUDA; }
   e = cudaMemcpy(c->blob_dev, blob.data(), o, cudaMemcpyHostToDevice);
   int st = cuda_status(e);
-  if (st == NBLDPC_OK) st = configure(c, 0, default_fpb(c));
+  if (st == NBLDPC_OK) st = configure(c, default_variant(q), default_fpb(c));
   if (st != NBLDPC_OK) {
     cudaFree(c->blob_dev);
     delete c;
