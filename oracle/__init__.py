@@ -49,6 +49,9 @@ def lib():
             L.orc_decode.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                      i32p, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, u8p, i32p, u8p]
+            L.orc_decode_cap.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
+                                         i32p, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, u8p, i32p, u8p]
             L.orc_syndrome_ok.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                           i32p, i32p, i32p, u8p, ctypes.c_int, u8p]
             _lib = L
@@ -95,8 +98,10 @@ def _code_arrays(code):
             np.ascontiguousarray(code.coef, np.int32))
 
 
-def decode(code, gamma: np.ndarray, max_iters: int, early_stop: int, threads: int = 1):
-    """(symbols [F, N] uint8, iterations [F] int32, ok [F] uint8) for gamma [F, N, q] uint8."""
+def decode(code, gamma: np.ndarray, max_iters: int, early_stop: int, threads: int = 1, cap: int = 255):
+    """(symbols [F, N] uint8, iterations [F] int32, ok [F] uint8) for gamma [F, N, q] uint8.
+
+    cap: saturation of the variable-node messages (255: 8-bit messages; 65535: 16-bit)."""
     g = np.ascontiguousarray(gamma, np.uint8)
     f = g.shape[0]
     assert g.shape[1:] == (code.n, code.q)
@@ -109,11 +114,11 @@ def decode(code, gamma: np.ndarray, max_iters: int, early_stop: int, threads: in
     def run(lo, hi):
         if hi <= lo:
             return 0
-        return L.orc_decode(code.q, code.poly, code.n, code.m, _p(rp, ctypes.c_int32),
-                            _p(ci, ctypes.c_int32), _p(cf, ctypes.c_int32),
-                            _p(g[lo:hi], ctypes.c_uint8), hi - lo, max_iters, early_stop,
-                            _p(sym[lo:hi], ctypes.c_uint8), _p(its[lo:hi], ctypes.c_int32),
-                            _p(ok[lo:hi], ctypes.c_uint8))
+        return L.orc_decode_cap(code.q, code.poly, code.n, code.m, _p(rp, ctypes.c_int32),
+                                _p(ci, ctypes.c_int32), _p(cf, ctypes.c_int32),
+                                _p(g[lo:hi], ctypes.c_uint8), hi - lo, max_iters, early_stop, cap,
+                                _p(sym[lo:hi], ctypes.c_uint8), _p(its[lo:hi], ctypes.c_int32),
+                                _p(ok[lo:hi], ctypes.c_uint8))
 
     if threads <= 1 or f <= 1:
         rc = run(0, f)

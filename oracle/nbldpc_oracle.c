@@ -214,13 +214,15 @@ static int check_code(int q, int n, int m, const int32_t *row_ptr, const int32_t
 /*
  * Decode `frames` frames.  gamma: [frames][n][q] (symbol value is the index).
  * Outputs: out_sym [frames][n], out_iters [frames], out_ok [frames].
+ * cap: the saturation of the variable-node messages (255 for the 8-bit
+ * messages of the main reading; 65535 for the 16-bit-message comparison).
  * Returns 0, or -1 on invalid arguments (nothing written).
  */
-int orc_decode(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
-               const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
-               uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok) {
+int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
+                   const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
+                   int cap, uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok) {
   gf_t g;
-  if (gf_build(&g, q, poly) || frames < 0 || max_iters < 0) return -1;
+  if (gf_build(&g, q, poly) || frames < 0 || max_iters < 0 || cap < 1) return -1;
   if (check_code(q, n, m, row_ptr, col_idx, coef)) return -1;
   const int E = row_ptr[m];
 
@@ -279,7 +281,7 @@ int orc_decode(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const
         }
         /* VNP for every variable node:
          *   alpha'_{m,n}(x) = gamma_n(x) + sum over i in S_c(n)\m of beta_{i,n}(x)
-         *   alpha_{m,n}(x)  = alpha'(x) - min_x alpha'(x), saturated at 255   */
+         *   alpha_{m,n}(x)  = alpha'(x) - min_x alpha'(x), saturated at cap   */
         for (int c = 0; c < n; c++) {
           for (int a = vptr[c]; a < vptr[c + 1]; a++) {
             int e = vedge[a];
@@ -293,7 +295,7 @@ int orc_decode(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const
             }
             for (int x = 0; x < q; x++) {
               int v = alpha[(size_t)e * q + x] - mn;
-              alpha[(size_t)e * q + x] = v > 255 ? 255 : v;
+              alpha[(size_t)e * q + x] = v > cap ? cap : v;
             }
           }
           /* a posteriori information and hard decision */
@@ -319,6 +321,14 @@ int orc_decode(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const
   free(vdeg); free(vptr); free(vfill); free(vedge); free(alpha); free(beta);
   free(F); free(B); free(ap); free(bp); free(hrow); free(chat); free(ap_sum);
   return 0;
+}
+
+/* The main reading: 8-bit messages, saturation at 255. */
+int orc_decode(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
+               const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
+               uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok) {
+  return orc_decode_cap(q, poly, n, m, row_ptr, col_idx, coef, gamma, frames, max_iters, early_stop, 255,
+                        out_sym, out_iters, out_ok);
 }
 
 /* Syndrome check of given words (for tests). */

@@ -136,9 +136,9 @@ def test_check_update_matches_brute_force(oracle_lib, q, d):
 
 
 # ---------------------------------------------------------------- P3 binary min-sum
-def binary_min_sum(code, gamma, max_iters, early_stop):
+def binary_min_sum(code, gamma, max_iters, early_stop, cap=255):
     """Textbook flooding min-sum on integer LLRs (no offset, no scaling),
-    variable-to-check magnitudes capped at 255; L = gamma(1) - gamma(0)."""
+    variable-to-check magnitudes capped at `cap`; L = gamma(1) - gamma(0)."""
     rp, ci = code.row_ptr, code.col_idx
     E = int(rp[-1])
     row_of = np.repeat(np.arange(code.m), np.diff(rp))
@@ -167,7 +167,7 @@ def binary_min_sum(code, gamma, max_iters, early_stop):
                 tot = lch.copy()
                 np.add.at(tot, ci, c2v)
                 t = tot[ci] - c2v
-                v2c = np.sign(t) * np.minimum(np.abs(t), 255)
+                v2c = np.sign(t) * np.minimum(np.abs(t), cap)
                 chat = (tot < 0).astype(np.int64)
                 it = k
                 ok = ok_of(chat)
@@ -333,3 +333,30 @@ def test_vnp_saturates_at_255(oracle_lib):
     assert sym.tolist() == [[0, 0, 0]] and its.tolist() == [2] and ok.tolist() == [1]
     ws, wi, wo = binary_min_sum(code, gamma, 2, 0)
     assert np.array_equal(sym, ws)
+
+
+# ---------------------------------------------------------------- 16-bit messages
+@pytest.mark.parametrize("dv,dc,n", [(3, 6, 60), (2, 4, 48)])
+def test_q2_wide_messages_are_binary_min_sum_with_the_wide_cap(oracle_lib, dv, dc, n):
+    code = I.make_regular_code(2, n, dv, dc, seed=91 + n + dv)
+    rng = np.random.default_rng(n + 7 * dv)
+    f = 30
+    gamma = np.zeros((f, n, 2), np.uint8)
+    hard = rng.integers(0, 2, (f, n))
+    gamma[np.arange(f)[:, None], np.arange(n)[None, :], 1 - hard] = rng.integers(100, 256, (f, n))
+    for cap in (255, 65535):
+        sym, its, ok = oracle_lib.decode(code, gamma, 15, 0, cap=cap)
+        ws, wi, wo = binary_min_sum(code, gamma, 15, 0, cap=cap)
+        assert np.array_equal(sym, ws) and np.array_equal(its, wi) and np.array_equal(ok, wo)
+
+
+def test_wide_cap_never_binds_for_column_degree_two(oracle_lib):
+    """With column degree 2 a message grows by at most max(gamma) per iteration
+    (alpha = gamma + beta - min and beta <= the largest incoming alpha), so
+    with gamma <= 63 and 30 iterations 16-bit messages equal unbounded ones."""
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    g = I.make_batch(code, 1.0, 31, 6).gamma.numpy()
+    a = oracle_lib.decode(code, g, 30, 0, cap=65535)
+    b = oracle_lib.decode(code, g, 30, 0, cap=1 << 30)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
