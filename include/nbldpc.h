@@ -215,6 +215,22 @@ int nbldpc_code_autotune(nbldpc_code *code, const uint8_t *gamma_dev, int frames
                          nbldpc_tune_result *results, int max_results, int *n_results);
 
 /*
+ * ---- Message width ---------------------------------------------------------
+ * 8 bits (the default) keeps every message as one byte per symbol saturated at
+ * 255 (the variable-node cap of the main reading).  16 bits keeps two bytes per
+ * symbol saturated at 65535: the counterpart of the paper's comparison of
+ * 8-bit and 32-bit integer messages (Sec. 5).  For column degree 2 and inputs
+ * <= 63 a message grows by at most 63 per iteration, so within 1000
+ * iterations the 16-bit cap is never reached and the results equal those of
+ * unbounded integer messages.  Results depend on the width (through the cap);
+ * each width is exact against the CPU oracle run with the same cap.  The
+ * workspace doubles at 16 bits; mixed-code batches accept 8-bit codes only
+ * (NBLDPC_ERR_UNSUPPORTED otherwise).
+ */
+int nbldpc_code_set_message_bits(nbldpc_code *code, int bits);   /* bits: 8 or 16 */
+int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
+
+/*
  * Size of the fixed device array that nbldpc_decode_noalloc works in.
  */
 #define NBLDPC_NOALLOC_SCRATCH_BYTES (32u << 20)

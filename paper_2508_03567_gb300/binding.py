@@ -30,7 +30,8 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_workspace_size", "nbldpc_decode", "nbldpc_decode_host_workspace_size",
             "nbldpc_decode_host", "nbldpc_decode_batch_workspace_size", "nbldpc_decode_batch",
             "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
-            "nbldpc_code_autotune", "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
+            "nbldpc_code_autotune", "nbldpc_code_set_message_bits", "nbldpc_code_get_message_bits",
+            "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
 NBLDPC_MAX_BATCH_JOBS = 32
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_decode_batch.argtypes = [jp, ctypes.c_int, vp, sz, vp]
             L.nbldpc_code_get_tuning.argtypes = [vp, ip, ip]
             L.nbldpc_code_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.nbldpc_code_set_message_bits.argtypes = [vp, ctypes.c_int]
+            L.nbldpc_code_get_message_bits.argtypes = [vp, ip]
             L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]
@@ -240,6 +243,16 @@ def nbldpc_code_set_tuning(handle: int, variant: int, frames_per_block: int) -> 
     _check(lib().nbldpc_code_set_tuning(handle, int(variant), int(frames_per_block)), "nbldpc_code_set_tuning")
 
 
+def nbldpc_code_set_message_bits(handle: int, bits: int) -> None:
+    _check(lib().nbldpc_code_set_message_bits(handle, int(bits)), "nbldpc_code_set_message_bits")
+
+
+def nbldpc_code_get_message_bits(handle: int) -> int:
+    b = ctypes.c_int()
+    _check(lib().nbldpc_code_get_message_bits(handle, ctypes.byref(b)), "nbldpc_code_get_message_bits")
+    return b.value
+
+
 def nbldpc_code_autotune_workspace_size(handle: int, frames: int) -> int:
     b = ctypes.c_size_t()
     _check(lib().nbldpc_code_autotune_workspace_size(handle, int(frames), ctypes.byref(b)),
@@ -288,6 +301,12 @@ class Decoder:
         ws = torch.empty(nbldpc_code_autotune_workspace_size(self.handle, f), dtype=torch.uint8,
                          device=gamma.device)
         return nbldpc_code_autotune(self.handle, gamma, f, max_iters, ws)
+
+    def set_message_bits(self, bits: int) -> None:
+        nbldpc_code_set_message_bits(self.handle, bits)
+
+    def message_bits(self) -> int:
+        return nbldpc_code_get_message_bits(self.handle)
 
     def tuning(self):
         return nbldpc_code_get_tuning(self.handle)

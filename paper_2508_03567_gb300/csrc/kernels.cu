@@ -13,14 +13,18 @@
 
 namespace nbldpc {
 
-// Address of the decode kernel for layout variant v of this unit's field order.
-const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v) {
+// Address of the decode kernel for layout variant v and mb-byte messages of
+// this unit's field order.
+const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb) {
 #if NBLDPC_KQ == 0
   (void)v;
-  return reinterpret_cast<const void*>(&mma_decode_kernel<0, -1>);
+  return mb == 1 ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
 #else
-  return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1>)
-           : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0>);
+  if (mb == 2)
+    return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 2>)
+             : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 2>);
+  return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1>)
+           : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1>);
 #endif
 }
 

@@ -151,7 +151,7 @@ template <class g> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
 // xh = r ^ (s << TB), which makes the B register index r ^ t independent of
 // the lane and lets the final reduce-scatter keep and send fixed slots.
 // Inputs and output must not alias; the caller syncs the group afterwards.
-template <class g>
+template <class g, bool FMA_MAX>
 __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
                                         uint16_t* __restrict__ C, const ConvLane& ln, unsigned gmask) {
   uint32_t aown[g::AWN];
@@ -192,7 +192,7 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
       for (int r = 0; r < g::XN; ++r)
 #pragma unroll
         for (int t = 0; t < g::AWN; ++t) {
-          const uint32_t m = (r * g::AWN + t < FmaMax<g>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
+          const uint32_t m = (FMA_MAX && r * g::AWN + t < FmaMax<g>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
                                                               : vmax2(a[t], bl[dd][r ^ t]);
           acc[r] = (d == 0 && t == 0) ? m : vmin2(acc[r], m);
         }
@@ -248,8 +248,10 @@ struct LaunchParams {
 
 template <int Q> __host__ __device__ constexpr int vec_bytes() { return (2 * Q + 15) / 16 * 16; }
 
-template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax) {
-  return ((dmax * Q + 15) / 16) * 16 + (2 * dmax + 3) * vec_bytes<Q>();
+// per-group shared scratch: the d incoming rows (q symbols of mb bytes each)
+// and 2*dmax+3 16-bit vectors
+template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax, int mb = 1) {
+  return ((dmax * Q * mb + 15) / 16) * 16 + (2 * dmax + 3) * vec_bytes<Q>();
 }
 
 // named barrier over the threads of one frame slot (ids 1..fpb)
@@ -342,11 +344,13 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
 // slot's message area ([nnz][q] bytes).
-template <class g>
+template <class g, int MB>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
   constexpr int PW = g::PW;
+  constexpr int RS = Q * MB;                 // bytes of one message row
+  static_assert(MB == 1 || MB == 2, "message bytes");
   const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
   const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
   const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.row_ptr);
@@ -394,8 +398,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   }
 
   unsigned char* gs = scratch + (size_t)grp * job.group_bytes;
-  uint8_t* stage = gs;                                                   // [dmax][q] bytes
-  unsigned char* vecs = gs + ((job.dmax * Q + 15) / 16) * 16;
+  uint8_t* stage = gs;                                                   // [dmax][q * MB] bytes
+  unsigned char* vecs = gs + ((job.dmax * RS + 15) / 16) * 16;
   auto vec = [&](int i) { return reinterpret_cast<uint32_t*>(vecs + (size_t)i * g::VB); };
   auto vec16 = [&](int i) { return reinterpret_cast<uint16_t*>(vecs + (size_t)i * g::VB); };
   // vectors: P_j = vec(j), F_j = vec(dmax + j), B ping-pong = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
@@ -407,6 +411,51 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     // Values are 16-bit halves of 32-bit words: every sum stays below 2^16
     // (at most 255 * (column degree + 1)), so plain 32-bit adds and
     // subtractions never carry or borrow across the halves.
+    // 16-bit messages: the same pass on 32-bit sums, one symbol per register
+    auto vnp_wide = [&](bool first, bool want_alpha) {
+      constexpr int NB = g::VBPL;
+      for (int vn = vgrp; vn < job.n; vn += nvgroups) {
+        int S[NB];
+        const uint8_t* gr = gam + (size_t)vn * Q + vgl * NB;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) S[i] = gr[i];
+        const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
+        if (!first) {
+          for (int k = k0; k < k1; ++k) {
+            const uint16_t* br = reinterpret_cast<const uint16_t*>(X + (size_t)vn_edge[k] * RS) + vgl * NB;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) S[i] += br[i];
+          }
+        }
+        int key = 0x7FFFFFFF;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) key = min(key, (S[i] << 8) | (vgl * NB + i));
+        key = group_min<g::VG>(key, vmask);
+        if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
+        if (!first && want_alpha) {
+          for (int k = k0; k < k1; ++k) {
+            uint16_t* row = reinterpret_cast<uint16_t*>(X + (size_t)vn_edge[k] * RS) + vgl * NB;
+            int t[NB];
+            int mn = 0x7FFFFFFF;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) { t[i] = S[i] - row[i]; mn = min(mn, t[i]); }
+            mn = group_min<g::VG>(mn, vmask);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) row[i] = (uint16_t)min(65535, t[i] - mn);
+          }
+        }
+      }
+    };
+
+    // 16-bit messages start from alpha^(0) = gamma widened into every edge row
+    auto init_wide = [&]() {
+      const int nnz = row_ptr[job.m];
+      for (int i = stid; i < nnz * Q; i += nthr) {
+        const int e = i / Q, a = i % Q;
+        reinterpret_cast<uint16_t*>(X)[i] = gam[(size_t)edge_col[e] * Q + a];
+      }
+    };
+
     auto vnp = [&](bool first, bool want_alpha) {
       for (int vn = vgrp; vn < job.n; vn += nvgroups) {
         uint32_t S[g::VW];
@@ -478,7 +527,17 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       for (int r = grp; r < job.m; r += ngroups) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
         // stage incoming alpha rows (alpha^(0) = gamma on the first pass)
-        if constexpr (Q >= 16) {
+        if constexpr (MB == 2) {
+          constexpr int CH = RS / 16 > 0 ? RS / 16 : 1, CB = RS / CH;   // chunks of CB bytes
+          for (int i = gl; i < d * CH; i += g::G) {
+            const int j = i / CH, c = i % CH;
+            const uint8_t* src = X + (size_t)(e0 + j) * RS + c * CB;
+            uint8_t* dst = stage + j * RS + c * CB;
+            if constexpr (CB == 16) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+            else if constexpr (CB == 8) *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+            else *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<const uint32_t*>(src);
+          }
+        } else if constexpr (Q >= 16) {
           constexpr int CH = Q / 16;
           for (int i = gl; i < d * CH; i += g::G) {
             const int j = i / CH, c = i % CH;
@@ -496,7 +555,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         // permutation: P_j(y) = alpha_j(h_j^-1 y), 16-bit natural order
         for (int j = 0; j < d; ++j) {
           const int lhinv = edge_lhi[e0 + j];
-          const uint8_t* a = stage + j * Q;
+          const uint8_t* a = stage + j * RS;
+          const uint16_t* a16 = reinterpret_cast<const uint16_t*>(a);
           uint32_t* P = vec(j);
 #pragma unroll
           for (int i = 0; i < PW; ++i) {
@@ -504,7 +564,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
             if (PW * g::G == g::W || w < g::W) {
               const int s0 = (py_nz0 >> i) & 1 ? exp2[((py_log0 >> (8 * i)) & 0xFF) + lhinv] : 0;
               const int s1 = exp2[((py_log1 >> (8 * i)) & 0xFF) + lhinv];
-              P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
+              if constexpr (MB == 2) P[w] = (uint32_t)a16[s0] | ((uint32_t)a16[s1] << 16);
+              else P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
             }
           }
         }
@@ -516,12 +577,18 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 #pragma unroll
           for (int i = 0; i < g::BPL; ++i)
             out[i] = R16[(da_mask >> i) & 1 ? exp2[((da_log >> (8 * i)) & 0xFF) + lh] : 0];
-          store_bytes<g::BPL>(X + (size_t)e * Q + gl * g::BPL, out);
+          if constexpr (MB == 2) {
+            uint16_t* row = reinterpret_cast<uint16_t*>(X + (size_t)e * RS) + gl * g::BPL;
+#pragma unroll
+            for (int i = 0; i < g::BPL; ++i) row[i] = (uint16_t)out[i];
+          } else {
+            store_bytes<g::BPL>(X + (size_t)e * Q + gl * g::BPL, out);
+          }
         };
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
         int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<g>(vec(fprev), vec(j), vec16(job.dmax + j), cl, gmask);
+          mm_conv<g, MB == 1>(vec(fprev), vec(j), vec16(job.dmax + j), cl, gmask);
           group_sync<g::G>(gmask);
           fprev = job.dmax + j;
         }
@@ -532,11 +599,11 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         for (int j = d - 2; j >= 1; --j) {
           const int fj = (j == 1) ? 0 : job.dmax + j - 1;
           const int rv = 2 * job.dmax + 2;
-          mm_conv<g>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
+          mm_conv<g, MB == 1>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
           group_sync<g::G>(gmask);
           depermute(vec16(rv), e0 + j);
           const int bn = 2 * job.dmax + pp;
-          mm_conv<g>(vec(bcur), vec(j), vec16(bn), cl, gmask);
+          mm_conv<g, MB == 1>(vec(bcur), vec(j), vec16(bn), cl, gmask);
           group_sync<g::G>(gmask);
           bcur = bn;
           pp ^= 1;
@@ -547,15 +614,19 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     };
 
     // ---- decode one frame
-    vnp(true, false);                // c^(0) = argmin gamma
+    if constexpr (MB == 2) vnp_wide(true, false); else vnp(true, false);   // c^(0) = argmin gamma
     slot_sync(bar_id, nthr);
     bool ok = syndrome_ok();
     int iters = 0;
     if (!(job.early_stop && ok)) {
-      for (int k = 1; k <= job.max_iters; ++k) {
-        cnp(k == 1);
+      if constexpr (MB == 2) {
+        init_wide();
         slot_sync(bar_id, nthr);
-        vnp(false, k < job.max_iters);
+      }
+      for (int k = 1; k <= job.max_iters; ++k) {
+        cnp(MB == 1 && k == 1);
+        slot_sync(bar_id, nthr);
+        if constexpr (MB == 2) vnp_wide(false, k < job.max_iters); else vnp(false, k < job.max_iters);
         slot_sync(bar_id, nthr);
         iters = k;
         ok = syndrome_ok();
@@ -584,19 +655,20 @@ template <int QSEL, int VSEL> struct MinBlocks {
 };
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
-template <int Q, int VSEL>
+template <int Q, int VSEL, int MB>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                                uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   if constexpr (VSEL >= 0) {
-    decode_frame<Geo<Q, VSEL>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, VSEL>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (job.variant == 0) {
-    decode_frame<Geo<Q, 0>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 0>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else {
-    decode_frame<Geo<Q, 1>>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 1>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   }
 }
 
-template <int QSEL, int VSEL>
+// MB: message bytes per symbol (1: 8-bit messages; 2: 16-bit, single-field kernels only).
+template <int QSEL, int VSEL, int MB>
 __global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
@@ -628,17 +700,17 @@ __global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kern
       slot_sync(bar_id, nthr);
     }
     if constexpr (QSEL != 0) {
-      decode_variant<QSEL, VSEL>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      decode_variant<QSEL, VSEL, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
     } else {
       switch (job.q) {
-        case 2: decode_variant<2, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 4: decode_variant<4, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 8: decode_variant<8, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 16: decode_variant<16, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 32: decode_variant<32, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 64: decode_variant<64, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        case 128: decode_variant<128, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
-        default: decode_variant<256, -1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 2: decode_variant<2, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 4: decode_variant<4, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 8: decode_variant<8, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 16: decode_variant<16, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 32: decode_variant<32, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 64: decode_variant<64, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        case 128: decode_variant<128, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
+        default: decode_variant<256, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;
       }
     }
     slot_sync(bar_id, nthr);

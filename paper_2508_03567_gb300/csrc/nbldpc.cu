@@ -41,6 +41,7 @@ struct nbldpc_code {
   unsigned char* blob_dev = nullptr;
   nbldpc::CodeBlob off{};
   int variant = 0;                     // layout variant used by every decode of this code
+  int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
   Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
   std::mutex mu;                       // guards the lazily created copy stream
   cudaStream_t side = nullptr;         // second stream for nbldpc_decode_host
@@ -83,31 +84,32 @@ bool build_field(int q, uint32_t poly, std::vector<uint8_t>& exp2, std::vector<u
 }  // namespace
 
 namespace nbldpc {   // defined in kernels.cu, one translation unit per field order
-const void* kernel_q0(int v);
-const void* kernel_q2(int v);
-const void* kernel_q4(int v);
-const void* kernel_q8(int v);
-const void* kernel_q16(int v);
-const void* kernel_q32(int v);
-const void* kernel_q64(int v);
-const void* kernel_q128(int v);
-const void* kernel_q256(int v);
+const void* kernel_q0(int v, int mb);
+const void* kernel_q2(int v, int mb);
+const void* kernel_q4(int v, int mb);
+const void* kernel_q8(int v, int mb);
+const void* kernel_q16(int v, int mb);
+const void* kernel_q32(int v, int mb);
+const void* kernel_q64(int v, int mb);
+const void* kernel_q128(int v, int mb);
+const void* kernel_q256(int v, int mb);
 }  // namespace nbldpc
 
 namespace {
 
-// kernel compiled for one field order and layout variant, or for all of them (q = 0)
-const void* kernel_for(int q, int v) {
+// kernel compiled for one field order, layout variant and message width, or
+// for every field order (q = 0, 8-bit messages)
+const void* kernel_for(int q, int v, int mb) {
   switch (q) {
-    case 0: return nbldpc::kernel_q0(-1);
-    case 2: return nbldpc::kernel_q2(v);
-    case 4: return nbldpc::kernel_q4(v);
-    case 8: return nbldpc::kernel_q8(v);
-    case 16: return nbldpc::kernel_q16(v);
-    case 32: return nbldpc::kernel_q32(v);
-    case 64: return nbldpc::kernel_q64(v);
-    case 128: return nbldpc::kernel_q128(v);
-    case 256: return nbldpc::kernel_q256(v);
+    case 0: return nbldpc::kernel_q0(-1, mb);
+    case 2: return nbldpc::kernel_q2(v, mb);
+    case 4: return nbldpc::kernel_q4(v, mb);
+    case 8: return nbldpc::kernel_q8(v, mb);
+    case 16: return nbldpc::kernel_q16(v, mb);
+    case 32: return nbldpc::kernel_q32(v, mb);
+    case 64: return nbldpc::kernel_q64(v, mb);
+    case 128: return nbldpc::kernel_q128(v, mb);
+    case 256: return nbldpc::kernel_q256(v, mb);
   }
   return nullptr;
 }
@@ -128,16 +130,16 @@ int group_lanes(int q, int v) {
   return 0;
 }
 
-int group_bytes(int q, int dmax) {
+int group_bytes(int q, int dmax, int mb) {
   switch (q) {
-    case 2: return nbldpc::group_scratch_bytes<2>(dmax);
-    case 4: return nbldpc::group_scratch_bytes<4>(dmax);
-    case 8: return nbldpc::group_scratch_bytes<8>(dmax);
-    case 16: return nbldpc::group_scratch_bytes<16>(dmax);
-    case 32: return nbldpc::group_scratch_bytes<32>(dmax);
-    case 64: return nbldpc::group_scratch_bytes<64>(dmax);
-    case 128: return nbldpc::group_scratch_bytes<128>(dmax);
-    case 256: return nbldpc::group_scratch_bytes<256>(dmax);
+    case 2: return nbldpc::group_scratch_bytes<2>(dmax, mb);
+    case 4: return nbldpc::group_scratch_bytes<4>(dmax, mb);
+    case 8: return nbldpc::group_scratch_bytes<8>(dmax, mb);
+    case 16: return nbldpc::group_scratch_bytes<16>(dmax, mb);
+    case 32: return nbldpc::group_scratch_bytes<32>(dmax, mb);
+    case 64: return nbldpc::group_scratch_bytes<64>(dmax, mb);
+    case 128: return nbldpc::group_scratch_bytes<128>(dmax, mb);
+    case 256: return nbldpc::group_scratch_bytes<256>(dmax, mb);
   }
   return 0;
 }
@@ -145,16 +147,20 @@ int group_bytes(int q, int dmax) {
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
 std::mutex g_attr_mu;
-bool g_attr_done[64][17] = {};
+bool g_attr_done[64][33] = {};
 
-int kernel_slot(int q, int v) { return q == 0 ? 0 : 2 * (nbldpc::ilog2(q) - 1) + 1 + (v ? 1 : 0); }
+int kernel_slot(int q, int v, int mb) {
+  return q == 0 ? 0 : 1 + 4 * (nbldpc::ilog2(q) - 1) + 2 * (mb - 1) + (v ? 1 : 0);
+}
 
-int prepare_kernel(int q, int v, int dev, int smem_optin) {
+int prepare_kernel(int q, int v, int mb, int dev, int smem_optin) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
-  bool& done = g_attr_done[dev][kernel_slot(q, v)];
+  const void* k = kernel_for(q, v, mb);
+  if (!k) return NBLDPC_ERR_UNSUPPORTED;
+  bool& done = g_attr_done[dev][kernel_slot(q, v, mb)];
   if (!done) {
-    if (cudaFuncSetAttribute(kernel_for(q, v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
       return NBLDPC_ERR_CUDA;
     done = true;
   }
@@ -162,16 +168,16 @@ int prepare_kernel(int q, int v, int dev, int smem_optin) {
 }
 
 struct CodeNeeds {       // what one code asks of a frame slot
-  int q, variant, dmax, blob, n;
+  int q, variant, mb, dmax, blob, n;
   size_t msg;
 };
 
-CodeNeeds needs_of(const nbldpc_code* c, int variant) {
-  return CodeNeeds{c->q, variant, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q, 256)};
+CodeNeeds needs_of(const nbldpc_code* c, int variant, int mb) {
+  return CodeNeeds{c->q, variant, mb, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q * mb, 256)};
 }
 
-// Plan a launch of kernel (kq, kv) with fpb frame slots per block for a set of codes.
-int make_plan(int kq, int kv, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
+// Plan a launch of kernel (kq, kv, kmb) with fpb frame slots per block for a set of codes.
+int make_plan(int kq, int kv, int kmb, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -187,7 +193,7 @@ int make_plan(int kq, int kv, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   for (int i = 0; i < nc; ++i) {
     const int G = group_lanes(cs[i].q, cs[i].variant);
     if (G > nthr) return NBLDPC_ERR_UNSUPPORTED;
-    const int s = (nthr / G) * group_bytes(cs[i].q, cs[i].dmax);
+    const int s = (nthr / G) * group_bytes(cs[i].q, cs[i].dmax, cs[i].mb);
     if (s > scratch) scratch = s;
     if (cs[i].blob > pl.blob_cap) pl.blob_cap = cs[i].blob;
     if (cs[i].n > pl.n_cap) pl.n_cap = cs[i].n;
@@ -198,9 +204,10 @@ int make_plan(int kq, int kv, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   pl.slot_smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16 + scratch), 16);
   pl.smem = fpb * pl.slot_smem;
   if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
-  int st = prepare_kernel(kq, kv, dev, optin);
+  int st = prepare_kernel(kq, kv, kmb, dev, optin);
   if (st != NBLDPC_OK) return st;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv), pl.threads, pl.smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv, kmb), pl.threads, pl.smem) !=
+      cudaSuccess)
     return NBLDPC_ERR_CUDA;
   if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
   pl.grid_max = pl.per_sm * sms;
@@ -224,8 +231,8 @@ int default_fpb(const nbldpc_code* c) {
 
 int configure(nbldpc_code* c, int variant, int fpb) {
   Plan pl{};
-  const CodeNeeds need = needs_of(c, variant);
-  const int st = make_plan(c->q, variant, fpb, &need, 1, &pl);
+  const CodeNeeds need = needs_of(c, variant, c->mb);
+  const int st = make_plan(c->q, variant, c->mb, fpb, &need, 1, &pl);
   if (st != NBLDPC_OK) return st;
   c->variant = variant;
   c->plan = pl;
@@ -256,7 +263,7 @@ nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames,
   j.dmax = c->dmax;
   j.variant = c->variant;
   j.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
-  j.group_bytes = group_bytes(c->q, c->dmax);
+  j.group_bytes = group_bytes(c->q, c->dmax, c->mb);
   j.frames = frames;
   j.max_iters = max_iters;
   j.early_stop = early_stop ? 1 : 0;
@@ -291,7 +298,7 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
   lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant), c->plan, lp, grid_for(c->plan, frames), ws,
+  return launch_plan(kernel_for(c->q, c->variant, c->mb), c->plan, lp, grid_for(c->plan, frames), ws,
                      reinterpret_cast<uint8_t*>(ws) + 256, st);
 }
 
@@ -347,7 +354,8 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
   lp.jobs[0] = job_desc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, 0);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant), pl, lp, grid, scratch, reinterpret_cast<uint8_t*>(scratch) + 256,
+  return launch_plan(kernel_for(c->q, c->variant, c->mb), pl, lp, grid, scratch,
+                     reinterpret_cast<uint8_t*>(scratch) + 256,
                      reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
@@ -495,6 +503,21 @@ int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
   return configure(c, variant, frames_per_block);
 }
 
+int nbldpc_code_set_message_bits(nbldpc_code* c, int bits) {
+  if (!c || (bits != 8 && bits != 16)) return NBLDPC_ERR_ARG;
+  const int old = c->mb;
+  c->mb = bits / 8;
+  const int st = configure(c, c->variant, c->plan.fpb);
+  if (st != NBLDPC_OK) c->mb = old;
+  return st;
+}
+
+int nbldpc_code_get_message_bits(const nbldpc_code* c, int* bits) {
+  if (!c || !bits) return NBLDPC_ERR_ARG;
+  *bits = 8 * c->mb;
+  return NBLDPC_OK;
+}
+
 int nbldpc_decode_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
   if (!c || !bytes || frames < 0) return NBLDPC_ERR_ARG;
   *bytes = decode_ws_bytes(c, frames);
@@ -524,13 +547,14 @@ static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) 
   for (int i = 0; i < n_jobs; ++i) {
     const nbldpc_code* c = jobs[i].code;
     if (!c || jobs[i].frames < 0 || jobs[i].max_iters < 0) return NBLDPC_ERR_ARG;
-    need[i] = needs_of(c, c->variant);
+    if (c->mb != 1) return NBLDPC_ERR_UNSUPPORTED;   // mixed-code launches carry 8-bit messages
+    need[i] = needs_of(c, c->variant, 1);
     if (c->plan.fpb < fpb) fpb = c->plan.fpb;
     t += jobs[i].frames;
   }
   if (t > 0x7FFFFFFF) return NBLDPC_ERR_ARG;
   *total = (int)t;
-  return make_plan(0, -1, fpb, need, n_jobs, pl);
+  return make_plan(0, -1, 1, fpb, need, n_jobs, pl);
 }
 
 int nbldpc_decode_batch_workspace_size(const nbldpc_job* jobs, int n_jobs, size_t* bytes) {
@@ -564,7 +588,7 @@ int nbldpc_decode_batch(const nbldpc_job* jobs, int n_jobs, void* workspace_dev,
   lp.total_items = total;
   st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
-  return launch_plan(kernel_for(0, -1), pl, lp, grid_for(pl, total), workspace_dev,
+  return launch_plan(kernel_for(0, -1, 1), pl, lp, grid_for(pl, total), workspace_dev,
                      reinterpret_cast<uint8_t*>(workspace_dev) + 256, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
@@ -579,8 +603,8 @@ int nbldpc_code_autotune_workspace_size(const nbldpc_code* c, int frames, size_t
   for (int v = 0; v < 2; ++v)
     for (int fpb = 1; fpb <= 8; fpb *= 2) {
       Plan pl{};
-      const CodeNeeds need = needs_of(c, v);
-      if (make_plan(c->q, v, fpb, &need, 1, &pl) != NBLDPC_OK) continue;
+      const CodeNeeds need = needs_of(c, v, c->mb);
+      if (make_plan(c->q, v, c->mb, fpb, &need, 1, &pl) != NBLDPC_OK) continue;
       const size_t w = ws_bytes(pl, frames);
       if (w > mx) mx = w;
     }

@@ -81,3 +81,10 @@ def test_rejects_null_arguments(lib):
     sz = ctypes.c_size_t()
     assert L.nbldpc_decode_workspace_size(None, 1, ctypes.byref(sz)) == lib.NBLDPC_ERR_ARG
     assert L.nbldpc_decode(None, None, 1, 1, 1, None, None, None, None, 0, None) == lib.NBLDPC_ERR_ARG
+
+
+def test_message_width_arguments_are_checked(lib):
+    L = lib.lib()
+    assert L.nbldpc_code_set_message_bits(None, 8) == lib.NBLDPC_ERR_ARG
+    b = ctypes.c_int()
+    assert L.nbldpc_code_get_message_bits(None, ctypes.byref(b)) == lib.NBLDPC_ERR_ARG

@@ -344,3 +344,52 @@ def test_mixed_batch_replays_from_a_cuda_graph():
         for (code, _, mi, es), (dec, gd, sym, its, ok) in zip(specs, keep):
             want = oracle.decode(code, gd.cpu().numpy(), mi, es, threads=THREADS)
             assert_same([sym.cpu().numpy(), its.cpu().numpy(), ok.cpu().numpy()], want, f"replay {rnd}")
+
+
+# --------------------------------------------------------------- 16-bit messages
+WIDE = [("gf64_n576_dv2_dc4", None, 24, 1.5), ("gf32_n600_dv3_dc6", None, 24, 1.0),
+        ("gf256_n128_dv2_dc8", None, 8, 2.0), ("q2", (2, 60, 3, 6), 30, 0.0), ("q8", (8, 64, 3, 6), 24, 0.5),
+        ("q128", (128, 96, 2, 4), 12, 1.5)]
+
+
+@pytest.mark.parametrize("name,shape,frames,eb", WIDE)
+def test_sixteen_bit_messages_match_the_oracle_with_the_wide_cap(name, shape, frames, eb):
+    if shape is None:
+        code = I.workload_code(name)
+    else:
+        q, n, dv, dc = shape
+        code = I.make_regular_code(q, n, dv, dc, seed=13 * q + n)
+    g = I.make_batch(code, eb, 4040, frames).gamma.numpy()
+    if code.q == 2:   # large magnitudes: with column degree 3 the messages reach the 65535 cap
+        g = (g.astype(np.int32) * 4).clip(0, 255).astype(np.uint8)
+    dec = binding.Decoder.from_code(code)
+    dec.set_message_bits(16)
+    assert dec.message_bits() == 16
+    gd = torch.as_tensor(g).cuda()
+    for mi, early in ((25, 1), (12, 0)):
+        got = [t.cpu().numpy() for t in dec.decode(gd, mi, early)]
+        want = oracle.decode(code, g, mi, early, threads=THREADS, cap=65535)
+        assert_same(got, want, f"{name} 16-bit max_iters={mi} early={early}")
+    for v in (0, 1):
+        for fpb in (1, 2):
+            try:
+                dec.set_tuning(v, fpb)
+            except binding.NbldpcError:
+                continue
+            got = [t.cpu().numpy() for t in dec.decode(gd, 25, 1)]
+            assert_same(got, oracle.decode(code, g, 25, 1, threads=THREADS, cap=65535), f"{name} v{v} fpb{fpb}")
+    dec.set_message_bits(8)
+    got = [t.cpu().numpy() for t in dec.decode(gd, 25, 1)]
+    assert_same(got, oracle.decode(code, g, 25, 1, threads=THREADS), f"{name} back to 8-bit")
+
+
+def test_mixed_batch_rejects_sixteen_bit_codes():
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    dec = binding.Decoder.from_code(code)
+    dec.set_message_bits(16)
+    g = torch.zeros((2, code.n, code.q), dtype=torch.uint8, device="cuda")
+    out = (torch.empty((2, code.n), dtype=torch.uint8, device="cuda"), torch.empty(2, dtype=torch.int32, device="cuda"),
+           torch.empty(2, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(binding.NbldpcError) as ei:
+        binding.nbldpc_decode_batch_workspace_size([(dec.handle, g, 2, 5, 1, *out)])
+    assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
