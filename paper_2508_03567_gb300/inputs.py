@@ -288,9 +288,9 @@ def awgn(code: Code, seed: int, frame0: int, frames: int) -> torch.Tensor:
     return torch.from_numpy(np.concatenate(out, 0) if out else np.zeros((0, code.n, code.p)))
 
 
-def quantized_reliabilities(code: Code, codewords: torch.Tensor, noise: torch.Tensor,
-                            ebn0_db) -> torch.Tensor:
-    """gamma [F, N, q] uint8 from codewords [F, N] and unit noise [F, N, p].
+def _symbol_costs(code: Code, codewords: torch.Tensor, noise: torch.Tensor, ebn0_db) -> torch.Tensor:
+    """g [F, N, q] float64: sum of |LLR_i| over the bits i where symbol x differs
+    from the bitwise hard decision (BPSK bit 0 -> +1, AWGN, LLR = 2y / sigma^2).
 
     ebn0_db is one value for every frame or a float64 tensor [F] of per-frame values."""
     dev = codewords.device
@@ -314,8 +314,25 @@ def quantized_reliabilities(code: Code, codewords: torch.Tensor, noise: torch.Te
         w = 1 << i
         t[..., w:2 * w] = t[..., 0:w] + mag[..., i:i + 1]
     idx = torch.arange(q, device=dev) ^ hard[..., None]
-    g = torch.gather(t, -1, idx)
+    return torch.gather(t, -1, idx)
+
+
+def quantized_reliabilities(code: Code, codewords: torch.Tensor, noise: torch.Tensor,
+                            ebn0_db) -> torch.Tensor:
+    """gamma [F, N, q] uint8 from codewords [F, N] and unit noise [F, N, p]:
+    min(63, round(4 g)) of the symbol costs g (0 for the most likely symbol)."""
+    g = _symbol_costs(code, codewords, noise, ebn0_db)
     return torch.clamp(torch.round(4.0 * g), max=63.0).to(torch.uint8)
+
+
+def channel_probabilities(code: Code, codewords: torch.Tensor, noise: torch.Tensor,
+                          ebn0_db) -> torch.Tensor:
+    """p [F, N, q] float32: the symbol probabilities p(c_n = x | y_n), the product
+    of the independent bit probabilities, normalized to sum 1 (computed in
+    float64 as exp(-g) / sum exp(-g), then rounded to float32)."""
+    g = _symbol_costs(code, codewords, noise, ebn0_db)
+    w = torch.exp(-g)
+    return (w / w.sum(-1, keepdim=True)).to(torch.float32)
 
 
 def frame_ebn0(seed: int, frame0: int, frames: int, lo: float, hi: float) -> torch.Tensor:
@@ -331,15 +348,17 @@ def frame_ebn0(seed: int, frame0: int, frames: int, lo: float, hi: float) -> tor
 class Batch:
     gamma: torch.Tensor       # [F, N, q] uint8
     codewords: torch.Tensor   # [F, N] int64
+    prob: torch.Tensor | None = None   # [F, N, q] float32 channel probabilities (make_batch(prob=True))
 
 
 def make_batch(code: Code, ebn0_db, seed: int, frames: int, frame0: int = 0,
                device: str | torch.device = "cpu", noiseless: bool = False,
-               chunk: int = 4096) -> Batch:
+               chunk: int = 4096, prob: bool = False) -> Batch:
     """Frames [frame0, frame0+frames) of one (code, Eb/N0, seed) stream.
 
-    ebn0_db: one value, or a (lo, hi) pair for per-frame Eb/N0 uniform in [lo, hi)."""
-    gam, cws = [], []
+    ebn0_db: one value, or a (lo, hi) pair for per-frame Eb/N0 uniform in [lo, hi).
+    prob: also return the float32 channel probabilities of the same frames."""
+    gam, cws, prs = [], [], []
     for lo in range(0, frames, chunk):
         nf = min(chunk, frames - lo)
         info = info_symbols(code, seed, frame0 + lo, nf).to(device)
@@ -351,10 +370,13 @@ def make_batch(code: Code, ebn0_db, seed: int, frames: int, frame0: int = 0,
         eb = frame_ebn0(seed + 2, frame0 + lo, nf, *ebn0_db) if isinstance(ebn0_db, tuple) else ebn0_db
         gam.append(quantized_reliabilities(code, cw, nz, eb))
         cws.append(cw)
+        if prob:
+            prs.append(channel_probabilities(code, cw, nz, eb))
     if not gam:
         return Batch(torch.zeros((0, code.n, code.q), dtype=torch.uint8, device=device),
-                     torch.zeros((0, code.n), dtype=torch.int64, device=device))
-    return Batch(torch.cat(gam, 0), torch.cat(cws, 0))
+                     torch.zeros((0, code.n), dtype=torch.int64, device=device),
+                     torch.zeros((0, code.n, code.q), dtype=torch.float32, device=device) if prob else None)
+    return Batch(torch.cat(gam, 0), torch.cat(cws, 0), torch.cat(prs, 0) if prob else None)
 
 
 # ----------------------------------------------------------------------------
