@@ -56,9 +56,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed", "serving"],
+    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed", "serving", "width"],
                     help="gf64: the GF(64) N=576 headline step; mixed: the four-code batch, persistent vs "
-                         "plain; serving: Poisson request arrivals, continuous batching vs plain")
+                         "plain; serving: Poisson request arrivals, continuous batching vs plain; width: 8-bit "
+                         "against 16-bit messages (throughput and frame error rate)")
     ap.add_argument("--seconds", type=float, default=6.0, help="serving: arrival window per load point")
     ap.add_argument("--frames", type=int, default=None, help="frames per Eb/N0 point (default: 65536)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -399,6 +400,92 @@ def run_serving(args, ws, rank, local):
     return 0
 
 
+def run_width(args, ws, rank, local):
+    """8-bit against 16-bit messages on the same frames: decoded Mbit/s and
+    frame error rate (decided symbols against the transmitted codeword), for
+    the GF(64) (2,4) N=576 step and the GF(32) (3,6) N=600 code (three
+    messages per symbol, so the variable-node sums are larger)."""
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding, inputs as I
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    mhz, mhz_kind = sm_max_mhz()
+    peak = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
+    results = {}
+    with ClockSampler(local) as clk:
+        for name, fpp in ((WORKLOAD, args.frames or 65536), ("gf32_n600_dv3_dc6", args.frames or 65536)):
+            w = I.WORKLOADS[name]
+            code = I.workload_code(name)
+            gam, cws = [], []
+            for i, eb in enumerate(w["ebn0"]):
+                b = I.make_batch(code, eb, I.workload_seed(name, i) + 7919 * rank, fpp, device=dev, chunk=8192)
+                gam.append(b.gamma)
+                cws.append(b.codewords)
+            gamma = torch.cat(gam, 0).contiguous()
+            cw = torch.cat(cws, 0)
+            frames = gamma.shape[0]
+            sym = torch.empty((frames, code.n), dtype=torch.uint8, device=dev)
+            its = torch.empty((frames,), dtype=torch.int32, device=dev)
+            ok = torch.empty((frames,), dtype=torch.uint8, device=dev)
+            mi, es = w["max_iters"], w["early_stop"]
+            row = {"frames": frames, "ebn0_db": list(w["ebn0"]), "max_iters": mi}
+            for bits in (8, 16):
+                dec = binding.Decoder.from_code(code)
+                dec.set_message_bits(bits)
+                if not args.no_autotune:
+                    dec.autotune(gamma[: min(frames, 4096)], 3)
+                wsb = dec.workspace(frames, dev)
+
+                def step():
+                    binding.nbldpc_decode(dec.handle, gamma, frames, mi, es, sym, its, ok, wsb, stream=stream)
+
+                with torch.cuda.stream(stream):
+                    for _ in range(args.warmup):
+                        step()
+                torch.cuda.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                for a, b in ev:
+                    a.record(stream)
+                    step()
+                    b.record(stream)
+                torch.cuda.synchronize()
+                t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+                its_h = its.cpu().numpy().astype(np.int64)
+                pairs = int(its_h.sum()) * pairs_per_frame_iter(code)
+                ach = 2 * pairs / (t / args.steps) / 1e9
+                row[f"{bits}bit"] = {
+                    "value": args.steps * frames * code.k * code.p / t / 1e6, "unit": "Mbit/s",
+                    "ms_per_step": 1e3 * t / args.steps,
+                    "fer": float((sym.to(torch.int64) != cw).any(1).float().mean()),
+                    "mean_iters": float(its_h.mean()), "tuning": list(dec.tuning()),
+                    "alu_frac": ach / peak}
+            results[name] = row
+    if rank != 0:
+        return 0
+    head = results[WORKLOAD]["16bit"]
+    line = {
+        "metric": "decoded info Mbit/s", "value": ws * head["value"], "unit": "Mbit/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} with 16-bit messages (value); 8-bit alongside; "
+                               "gf32_n600_dv3_dc6 both widths", "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "alu", "achieved": head["alu_frac"] * peak, "peak": peak, "unit": "Gop/s",
+                     "frac": head["alu_frac"], "traffic": None,
+                     "peak_kind": f"derived: 152 SMs x 256 u16 min/max ops/clk x {mhz:.0f} MHz ({mhz_kind})"},
+        "clocks": clk.summary(),
+        "gpu_launches": 2 * len(results) * args.steps,
+        "widths": results,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -408,6 +495,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "serving":
         return run_serving(args, ws, rank, local)
+    if args.workload == "width":
+        return run_width(args, ws, rank, local)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     import __graft_entry__
