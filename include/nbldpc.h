@@ -231,6 +231,61 @@ int nbldpc_code_set_message_bits(nbldpc_code *code, int bits);   /* bits: 8 or 1
 int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
 
 /*
+ * ---- FFT-based sum-product decoding (FFT-SPA, Alg. 1) -----------------------
+ *
+ * The paper's second decoder, in float arithmetic: messages are q symbol
+ * probabilities per edge; the check node multiplies the Walsh-Hadamard
+ * transforms (radix-2 transform over (Z_2)^p) of the permuted incoming
+ * messages and transforms back (divided by q); the variable node multiplies
+ * the channel probabilities with the other incoming messages and normalizes
+ * the result to sum 1; the decision is the symbol of largest a-posteriori
+ * product (lowest symbol on ties); the syndrome stop test precedes each
+ * iteration as in Alg. 2.  A check-node output below zero (transform
+ * rounding) is set to 0; a normalization whose sum is not positive gives the
+ * uniform vector 1/q.
+ *
+ * Supported codes: check degree <= 8 and column degree <= 8 (the FFT-SPA
+ * kernels keep a check's transformed messages in registers); other codes
+ * return NBLDPC_ERR_UNSUPPORTED from both calls.
+ */
+
+/* Device workspace nbldpc_fftspa_decode needs for `frames` frames, in bytes
+ * (one message slot of nnz*q floats per resident block, so the size
+ * saturates for large batches). */
+int nbldpc_fftspa_workspace_size(const nbldpc_code *code, int frames, size_t *bytes);
+
+/*
+ * Decode `frames` frames with FFT-SPA (Alg. 1), stream-ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  Returns
+ * after queueing.
+ *
+ *   prob_dev       device, [frames][n_cols][q] float, 16-byte aligned, read
+ *                  only: the channel probabilities p_n(x) of each symbol
+ *                  (non-negative; each row is used as given, no
+ *                  normalization is applied to it)
+ *   max_iters      I_max >= 0 (0: channel decision only)
+ *   early_stop     non-zero: stop a frame once its decision satisfies every check
+ *   out_sym_dev    device, [frames][n_cols] uint8: decided symbols
+ *   out_iters_dev  device, [frames] int32: iterations run
+ *   out_ok_dev     device, [frames] uint8: 1 if the returned symbols satisfy every check
+ *   out_app_dev    device, [frames][n_cols][q] float, 16-byte aligned, or
+ *                  NULL: the a-posteriori vectors of the returned decision,
+ *                  normalized to sum 1 (the channel probabilities, normalized,
+ *                  when no iteration ran)
+ *   workspace_dev  device, >= nbldpc_fftspa_workspace_size(code, frames)
+ *                  bytes, 16-byte aligned; scratch owned by the caller,
+ *                  contents undefined after the call; one decode at a time
+ *                  per workspace
+ *
+ * All device buffers are owned by the caller and must stay valid until the
+ * queued work completes.  frames == 0 queues nothing.  Each frame's outputs
+ * depend only on that frame's probabilities.
+ */
+int nbldpc_fftspa_decode(const nbldpc_code *code, const float *prob_dev, int frames, int max_iters,
+                         int early_stop, uint8_t *out_sym_dev, int32_t *out_iters_dev, uint8_t *out_ok_dev,
+                         float *out_app_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/*
  * Size of the fixed device array that nbldpc_decode_noalloc works in.
  */
 #define NBLDPC_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -31,6 +31,7 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_host", "nbldpc_decode_batch_workspace_size", "nbldpc_decode_batch",
             "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
             "nbldpc_code_autotune", "nbldpc_code_set_message_bits", "nbldpc_code_get_message_bits",
+            "nbldpc_fftspa_workspace_size", "nbldpc_fftspa_decode",
             "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
@@ -89,6 +90,9 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_code_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.nbldpc_code_set_message_bits.argtypes = [vp, ctypes.c_int]
             L.nbldpc_code_get_message_bits.argtypes = [vp, ip]
+            L.nbldpc_fftspa_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_fftspa_decode.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
+                                               vp, sz, vp]
             L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]
@@ -178,6 +182,23 @@ def nbldpc_decode(handle: int, gamma, frames: int, max_iters: int, early_stop: i
                              _ptr(out_sym), _ptr(out_iters), _ptr(out_ok), _ptr(workspace),
                              int(workspace_bytes), _stream_ptr(stream))
     _check(st, "nbldpc_decode")
+
+
+def nbldpc_fftspa_workspace_size(handle: int, frames: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_fftspa_workspace_size(handle, int(frames), ctypes.byref(b)), "nbldpc_fftspa_workspace_size")
+    return b.value
+
+
+def nbldpc_fftspa_decode(handle: int, prob, frames: int, max_iters: int, early_stop: int, out_sym, out_iters,
+                         out_ok, out_app, workspace, workspace_bytes: int | None = None, stream=None) -> None:
+    """Queue an FFT-SPA decode of device buffers on `stream` (out_app may be None)."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    st = lib().nbldpc_fftspa_decode(handle, _ptr(prob), int(frames), int(max_iters), int(early_stop),
+                                    _ptr(out_sym), _ptr(out_iters), _ptr(out_ok), _ptr(out_app),
+                                    _ptr(workspace), int(workspace_bytes), _stream_ptr(stream))
+    _check(st, "nbldpc_fftspa_decode")
 
 
 def nbldpc_decode_host(handle: int, gamma_host, frames: int, max_iters: int, early_stop: int,
@@ -280,6 +301,7 @@ class Decoder:
         self.handle = nbldpc_code_create(q, prim_poly, n_cols, n_rows, row_ptr, col_idx, coef)
         self.q, self.n, self.m, self.nnz = nbldpc_code_info(self.handle)
         self._ws = None
+        self._fws = None
 
     @classmethod
     def from_code(cls, code):
@@ -332,3 +354,24 @@ class Decoder:
         ws = self.workspace(f, dev)
         nbldpc_decode(self.handle, gamma, f, max_iters, early_stop, sym, its, ok, ws, stream=stream)
         return sym, its, ok
+
+    def fftspa_workspace(self, frames: int, device) -> torch.Tensor:
+        need = nbldpc_fftspa_workspace_size(self.handle, frames)
+        if self._fws is None or self._fws.numel() < need or self._fws.device != torch.device(device):
+            self._fws = torch.empty(need, dtype=torch.uint8, device=device)
+        return self._fws
+
+    def fftspa_decode(self, prob: torch.Tensor, max_iters: int, early_stop: int, want_app: bool = False,
+                      stream=None):
+        """FFT-SPA (Alg. 1): (symbols, iterations, ok[, app [F, N, q] float32]) on prob's device."""
+        assert prob.is_cuda and prob.dtype == torch.float32 and prob.is_contiguous()
+        f = prob.shape[0]
+        assert prob.shape[1:] == (self.n, self.q)
+        dev = prob.device
+        sym = torch.empty((f, self.n), dtype=torch.uint8, device=dev)
+        its = torch.empty((f,), dtype=torch.int32, device=dev)
+        ok = torch.empty((f,), dtype=torch.uint8, device=dev)
+        app = torch.empty((f, self.n, self.q), dtype=torch.float32, device=dev) if want_app else None
+        ws = self.fftspa_workspace(f, dev)
+        nbldpc_fftspa_decode(self.handle, prob, f, max_iters, early_stop, sym, its, ok, app, ws, stream=stream)
+        return (sym, its, ok, app) if want_app else (sym, its, ok)

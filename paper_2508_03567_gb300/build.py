@@ -1,7 +1,8 @@
 """Compile the CUDA decoder library (libnbldpc.so) in-tree for sm_103a.
 
-The kernel translation units (one per field order, plus the one serving every
-field order) compile in parallel; the host unit holds the C ABI.
+The kernel translation units (min-max: one per field order plus the one serving
+every field order; FFT-SPA: one per field order) compile in parallel; the host
+unit holds the C ABI.
 """
 from __future__ import annotations
 
@@ -16,6 +17,7 @@ LIB = os.path.join(HERE, "libnbldpc.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 CSRC = os.path.join(HERE, "csrc")
 KERNEL_UNITS = (0, 2, 4, 8, 16, 32, 64, 128, 256)
+FFT_UNITS = (2, 4, 8, 16, 32, 64, 128, 256)
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 
@@ -36,6 +38,7 @@ def _stale() -> bool:
 
 def _units():
     units = [(os.path.join(CSRC, "kernels.cu"), f"kernels_q{q}.o", [f"-DNBLDPC_KQ={q}"]) for q in KERNEL_UNITS]
+    units += [(os.path.join(CSRC, "fftspa.cu"), f"fftspa_q{q}.o", [f"-DNBLDPC_FQ={q}"]) for q in FFT_UNITS]
     units.append((os.path.join(CSRC, "nbldpc.cu"), "nbldpc.o", []))
     return units
 

@@ -11,10 +11,12 @@
 #include <new>
 #include <vector>
 
+#include "fftspa_kernels.cuh"
 #include "mma_kernels.cuh"
 
 static_assert(nbldpc::kMaxJobs == NBLDPC_MAX_BATCH_JOBS, "job table size");
 static_assert(sizeof(nbldpc::LaunchParams) < 32000, "kernel parameter space");
+static_assert(sizeof(nbldpc::FftParams) < 4000, "kernel parameter space");
 
 namespace {
 
@@ -43,6 +45,9 @@ struct nbldpc_code {
   int variant = 0;                     // layout variant used by every decode of this code
   int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
   Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
+  int fft_status = NBLDPC_ERR_UNSUPPORTED;   // FFT-SPA launch shape below valid when NBLDPC_OK
+  int fft_dc = 0, fft_dv = 0;          // degree buckets of the FFT-SPA kernel
+  Plan fft_plan{};
   std::mutex mu;                       // guards the lazily created copy stream
   cudaStream_t side = nullptr;         // second stream for nbldpc_decode_host
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -93,6 +98,14 @@ const void* kernel_q32(int v, int mb);
 const void* kernel_q64(int v, int mb);
 const void* kernel_q128(int v, int mb);
 const void* kernel_q256(int v, int mb);
+const void* fft_kernel_q2(int dc, int dv);
+const void* fft_kernel_q4(int dc, int dv);
+const void* fft_kernel_q8(int dc, int dv);
+const void* fft_kernel_q16(int dc, int dv);
+const void* fft_kernel_q32(int dc, int dv);
+const void* fft_kernel_q64(int dc, int dv);
+const void* fft_kernel_q128(int dc, int dv);
+const void* fft_kernel_q256(int dc, int dv);
 }  // namespace nbldpc
 
 namespace {
@@ -302,6 +315,97 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
                      reinterpret_cast<uint8_t*>(ws) + 256, st);
 }
 
+// ---- FFT-SPA (Alg. 1) --------------------------------------------------------
+const void* fft_kernel_for(int q, int dc, int dv) {
+  switch (q) {
+    case 2: return nbldpc::fft_kernel_q2(dc, dv);
+    case 4: return nbldpc::fft_kernel_q4(dc, dv);
+    case 8: return nbldpc::fft_kernel_q8(dc, dv);
+    case 16: return nbldpc::fft_kernel_q16(dc, dv);
+    case 32: return nbldpc::fft_kernel_q32(dc, dv);
+    case 64: return nbldpc::fft_kernel_q64(dc, dv);
+    case 128: return nbldpc::fft_kernel_q128(dc, dv);
+    case 256: return nbldpc::fft_kernel_q256(dc, dv);
+  }
+  return nullptr;
+}
+
+bool g_fft_attr_done[64][8][2][3] = {};   // device, log2(q) - 1, check-degree bucket, column-degree bucket
+
+// Launch shape of the FFT-SPA kernel for a code: degree buckets (check
+// degree <= 4 or 8, column degree <= 2, 4 or 8), shared memory (code blob,
+// decisions, control word), resident blocks, message slot of nnz * q floats.
+int fft_configure(nbldpc_code* c) {
+  const int dc = c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : 0);
+  const int dv = c->vmax <= 2 ? 2 : (c->vmax <= 4 ? 4 : (c->vmax <= 8 ? 8 : 0));
+  if (!dc || !dv) return NBLDPC_ERR_UNSUPPORTED;
+  const void* k = fft_kernel_for(c->q, dc, dv);
+  if (!k) return NBLDPC_ERR_UNSUPPORTED;
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
+  Plan pl{};
+  pl.fpb = 1;
+  pl.threads = kThreads;
+  pl.blob_cap = (int)round_up((size_t)c->off.bytes, 16);
+  pl.n_cap = (int)round_up((size_t)c->n, 16);
+  pl.slot_smem = pl.smem = pl.blob_cap + pl.n_cap + 16;
+  if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    bool& done = g_fft_attr_done[dev][nbldpc::ilog2(c->q) - 1][dc == 8][dv == 2 ? 0 : (dv == 4 ? 1 : 2)];
+    if (!done) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        return NBLDPC_ERR_CUDA;
+      done = true;
+    }
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, k, pl.threads, pl.smem) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
+  if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
+  pl.grid_max = pl.per_sm * sms;
+  pl.slot_bytes = round_up((size_t)c->nnz * c->q * sizeof(float), 256);
+  c->fft_plan = pl;
+  c->fft_dc = dc;
+  c->fft_dv = dv;
+  return NBLDPC_OK;
+}
+
+int fft_launch(const nbldpc_code* c, const float* prob, int frames, int max_iters, int early_stop, uint8_t* sym,
+               int32_t* iters, uint8_t* ok, float* app, void* ws, cudaStream_t st) {
+  const Plan& pl = c->fft_plan;
+  nbldpc::FftParams fp{};
+  fp.job.blob = c->blob_dev;
+  fp.job.off = c->off;
+  fp.job.prob = prob;
+  fp.job.out_sym = sym;
+  fp.job.out_iters = iters;
+  fp.job.out_ok = ok;
+  fp.job.out_app = app;
+  fp.job.q = c->q;
+  fp.job.n = c->n;
+  fp.job.m = c->m;
+  fp.job.frames = frames;
+  fp.job.max_iters = max_iters;
+  fp.job.early_stop = early_stop ? 1 : 0;
+  fp.counter = reinterpret_cast<unsigned int*>(ws);
+  fp.msg = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 256);
+  fp.slot_floats = pl.slot_bytes / sizeof(float);
+  fp.blob_cap = pl.blob_cap;
+  fp.n_cap = pl.n_cap;
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  void* args[] = {&fp};
+  e = cudaLaunchKernel(fft_kernel_for(c->q, c->fft_dc, c->fft_dv), dim3(grid_for(pl, frames)), dim3(pl.threads),
+                       args, (size_t)pl.smem, st);
+  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return NBLDPC_OK;
+}
+
 // ---- non-allocating decode (nbldpc_decode_noalloc) -------------------------
 // Fixed scratch for callers that cannot allocate: frame counter + message slots.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NBLDPC_NOALLOC_SCRATCH_BYTES];
@@ -462,6 +566,10 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   e = cudaMemcpy(c->blob_dev, blob.data(), o, cudaMemcpyHostToDevice);
   int st = cuda_status(e);
   if (st == NBLDPC_OK) st = configure(c, default_variant(q), default_fpb(c));
+  if (st == NBLDPC_OK) {
+    c->fft_status = fft_configure(c);
+    if (c->fft_status == NBLDPC_ERR_CUDA) st = NBLDPC_ERR_CUDA;
+  }
   if (st != NBLDPC_OK) {
     cudaFree(c->blob_dev);
     delete c;
@@ -536,6 +644,30 @@ int nbldpc_decode(const nbldpc_code* c, const uint8_t* gamma_dev, int frames, in
   if (st != NBLDPC_OK) return st;
   return launch(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev,
                 workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+// ---- FFT-SPA decoding ----------------------------------------------------------
+int nbldpc_fftspa_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
+  if (!c || frames < 0 || !bytes) return NBLDPC_ERR_ARG;
+  if (c->fft_status != NBLDPC_OK) return c->fft_status;
+  *bytes = ws_bytes(c->fft_plan, frames);
+  return NBLDPC_OK;
+}
+
+int nbldpc_fftspa_decode(const nbldpc_code* c, const float* prob_dev, int frames, int max_iters, int early_stop,
+                         uint8_t* out_sym_dev, int32_t* out_iters_dev, uint8_t* out_ok_dev, float* out_app_dev,
+                         void* workspace_dev, size_t workspace_bytes, void* cuda_stream) {
+  if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
+  if (c->fft_status != NBLDPC_OK) return c->fft_status;
+  if (frames == 0) return NBLDPC_OK;
+  if (!prob_dev || !out_sym_dev || !out_iters_dev || !out_ok_dev || !workspace_dev) return NBLDPC_ERR_ARG;
+  if (!aligned(prob_dev, 16) || !aligned(out_iters_dev, 4) || !aligned(workspace_dev, 16)) return NBLDPC_ERR_ARG;
+  if (out_app_dev && !aligned(out_app_dev, 16)) return NBLDPC_ERR_ARG;
+  if (workspace_bytes < ws_bytes(c->fft_plan, frames)) return NBLDPC_ERR_ARG;
+  int st = cuda_status(cudaGetLastError());
+  if (st != NBLDPC_OK) return st;
+  return fft_launch(c, prob_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, out_app_dev,
+                    workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 // ---- mixed-code batches -----------------------------------------------------

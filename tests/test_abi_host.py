@@ -88,3 +88,10 @@ def test_message_width_arguments_are_checked(lib):
     assert L.nbldpc_code_set_message_bits(None, 8) == lib.NBLDPC_ERR_ARG
     b = ctypes.c_int()
     assert L.nbldpc_code_get_message_bits(None, ctypes.byref(b)) == lib.NBLDPC_ERR_ARG
+
+
+def test_fftspa_arguments_are_checked_without_a_device(lib):
+    L = lib.lib()
+    b = ctypes.c_size_t()
+    assert L.nbldpc_fftspa_workspace_size(None, 4, ctypes.byref(b)) == lib.NBLDPC_ERR_ARG
+    assert L.nbldpc_fftspa_decode(None, None, 4, 5, 1, None, None, None, None, None, 0, None) == lib.NBLDPC_ERR_ARG
