@@ -12,9 +12,14 @@
 namespace nbldpc {
 
 // Address of the FFT-SPA kernel for check degrees <= dc (4 or 8) and column
-// degrees <= dv (2, 4 or 8) of this unit's field order; null otherwise.
-const void* NBLDPC_CAT(fft_kernel_q, NBLDPC_FQ)(int dc, int dv) {
+// degrees <= dv (2, 4 or 8) of this unit's field order, and its block size;
+// null otherwise.
+const void* NBLDPC_CAT(fft_kernel_q, NBLDPC_FQ)(int dc, int dv, int* threads) {
   constexpr int q = NBLDPC_FQ;
+  if (threads) {
+    *threads = dc == 4 ? (dv == 2 ? FftThreads<q, 4, 2>::v : dv == 4 ? FftThreads<q, 4, 4>::v : FftThreads<q, 4, 8>::v)
+                       : (dv == 2 ? FftThreads<q, 8, 2>::v : dv == 4 ? FftThreads<q, 8, 4>::v : FftThreads<q, 8, 8>::v);
+  }
   if (dc == 4) {
     if (dv == 2) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 4, 2>);
     if (dv == 4) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 4, 4>);

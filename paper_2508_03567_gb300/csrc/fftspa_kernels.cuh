@@ -1,6 +1,6 @@
 // FFT-based sum-product (FFT-SPA, Alg. 1) decoding of non-binary LDPC codes
 // over GF(2^p): device code for sm_103a, float arithmetic.  One persistent
-// 256-thread block decodes one frame at a time with the flooding schedule of
+// block per SM decodes one frame at a time with the flooding schedule of
 // Alg. 1 (check-node pass: permutation, transform, product, inverse
 // transform, depermutation; variable-node pass: product with the channel
 // probabilities, normalization, decision; syndrome), then takes the next
@@ -56,9 +56,6 @@ template <int Q_> struct FftGeo {
   static constexpr int VG = Q / RV;                   // lanes per variable vector (1..32)
 };
 
-// lowest set bit of r (r > 0), for compile-time index recurrences
-__host__ __device__ constexpr int low_bit(int r) { return (r & 1) ? 0 : 1 + low_bit(r >> 1); }
-
 // Walsh-Hadamard butterflies over the R register elements (index bits
 // 0..RB-1) then the G lanes of the group (bits RB..p-1): the pair
 // (a, b) at indices (x, x + 2^k) becomes (a + b, a - b).
@@ -91,11 +88,12 @@ __device__ __forceinline__ void wht(float (&v)[g::R], int gl, unsigned gmask) {
 template <class g>
 __device__ __forceinline__ void perm_index(int (&idx)[g::R], const uint8_t* exp2, int lhinv, int ly0, bool y0nz) {
   idx[0] = y0nz ? exp2[ly0 + lhinv] : 0;
-  int hb[g::RB > 0 ? g::RB : 1];
 #pragma unroll
-  for (int b = 0; b < g::RB; ++b) hb[b] = exp2[lhinv + b];   // h^-1 x^b
+  for (int b = 0; b < g::RB; ++b) {
+    const int hb = exp2[lhinv + b];                  // h^-1 x^b
 #pragma unroll
-  for (int r = 1; r < g::R; ++r) idx[r] = idx[r & (r - 1)] ^ hb[low_bit(r)];
+    for (int r = 0; r < (1 << b); ++r) idx[(1 << b) + r] = idx[r] ^ hb;
+  }
 }
 
 template <int N> __device__ __forceinline__ void load_vec(const float* p, float (&v)[N]) {
@@ -322,10 +320,18 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
 }
 
 // ---------------------------------------------------------------- the kernel
-// Persistent 256-thread blocks, one frame at a time; DC / DV bound the check
-// and column degrees of the code (register arrays of the two passes).
+// Threads of one block: one frame per SM, as many warps as the register
+// arrays allow (80 registers per thread: 24 warps; 128: 16 warps).  A single
+// frame's message slot per SM (nnz * q floats, 295 KB for GF(64) N=576) keeps
+// the resident message state of the whole GPU inside L2.
+template <int Q, int DC, int DV> struct FftThreads {
+  static constexpr int v = (DC <= 4 && Q < 256) ? 768 : 512;
+};
+
+// Persistent blocks, one frame at a time; DC / DV bound the check and column
+// degrees of the code (register arrays of the two passes).
 template <int Q, int DC, int DV>
-__global__ void __launch_bounds__(256, (DC <= 4 && !(Q >= 256 && DV >= 8)) ? 3 : 2) fftspa_decode_kernel(const __grid_constant__ FftParams p) {
+__global__ void __launch_bounds__(FftThreads<Q, DC, DV>::v, 1) fftspa_decode_kernel(const __grid_constant__ FftParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sblob = smem;
   uint8_t* chat = smem + p.blob_cap;

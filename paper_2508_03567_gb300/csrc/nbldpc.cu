@@ -98,14 +98,14 @@ const void* kernel_q32(int v, int mb);
 const void* kernel_q64(int v, int mb);
 const void* kernel_q128(int v, int mb);
 const void* kernel_q256(int v, int mb);
-const void* fft_kernel_q2(int dc, int dv);
-const void* fft_kernel_q4(int dc, int dv);
-const void* fft_kernel_q8(int dc, int dv);
-const void* fft_kernel_q16(int dc, int dv);
-const void* fft_kernel_q32(int dc, int dv);
-const void* fft_kernel_q64(int dc, int dv);
-const void* fft_kernel_q128(int dc, int dv);
-const void* fft_kernel_q256(int dc, int dv);
+const void* fft_kernel_q2(int dc, int dv, int* threads);
+const void* fft_kernel_q4(int dc, int dv, int* threads);
+const void* fft_kernel_q8(int dc, int dv, int* threads);
+const void* fft_kernel_q16(int dc, int dv, int* threads);
+const void* fft_kernel_q32(int dc, int dv, int* threads);
+const void* fft_kernel_q64(int dc, int dv, int* threads);
+const void* fft_kernel_q128(int dc, int dv, int* threads);
+const void* fft_kernel_q256(int dc, int dv, int* threads);
 }  // namespace nbldpc
 
 namespace {
@@ -316,16 +316,16 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
 }
 
 // ---- FFT-SPA (Alg. 1) --------------------------------------------------------
-const void* fft_kernel_for(int q, int dc, int dv) {
+const void* fft_kernel_for(int q, int dc, int dv, int* threads = nullptr) {
   switch (q) {
-    case 2: return nbldpc::fft_kernel_q2(dc, dv);
-    case 4: return nbldpc::fft_kernel_q4(dc, dv);
-    case 8: return nbldpc::fft_kernel_q8(dc, dv);
-    case 16: return nbldpc::fft_kernel_q16(dc, dv);
-    case 32: return nbldpc::fft_kernel_q32(dc, dv);
-    case 64: return nbldpc::fft_kernel_q64(dc, dv);
-    case 128: return nbldpc::fft_kernel_q128(dc, dv);
-    case 256: return nbldpc::fft_kernel_q256(dc, dv);
+    case 2: return nbldpc::fft_kernel_q2(dc, dv, threads);
+    case 4: return nbldpc::fft_kernel_q4(dc, dv, threads);
+    case 8: return nbldpc::fft_kernel_q8(dc, dv, threads);
+    case 16: return nbldpc::fft_kernel_q16(dc, dv, threads);
+    case 32: return nbldpc::fft_kernel_q32(dc, dv, threads);
+    case 64: return nbldpc::fft_kernel_q64(dc, dv, threads);
+    case 128: return nbldpc::fft_kernel_q128(dc, dv, threads);
+    case 256: return nbldpc::fft_kernel_q256(dc, dv, threads);
   }
   return nullptr;
 }
@@ -333,13 +333,15 @@ const void* fft_kernel_for(int q, int dc, int dv) {
 bool g_fft_attr_done[64][8][2][3] = {};   // device, log2(q) - 1, check-degree bucket, column-degree bucket
 
 // Launch shape of the FFT-SPA kernel for a code: degree buckets (check
-// degree <= 4 or 8, column degree <= 2, 4 or 8), shared memory (code blob,
-// decisions, control word), resident blocks, message slot of nnz * q floats.
+// degree <= 4 or 8, column degree <= 2, 4 or 8), block size (one frame per
+// SM), shared memory (code blob, decisions, control word), resident blocks,
+// message slot of nnz * q floats.
 int fft_configure(nbldpc_code* c) {
   const int dc = c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : 0);
   const int dv = c->vmax <= 2 ? 2 : (c->vmax <= 4 ? 4 : (c->vmax <= 8 ? 8 : 0));
   if (!dc || !dv) return NBLDPC_ERR_UNSUPPORTED;
-  const void* k = fft_kernel_for(c->q, dc, dv);
+  int threads = 0;
+  const void* k = fft_kernel_for(c->q, dc, dv, &threads);
   if (!k) return NBLDPC_ERR_UNSUPPORTED;
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -349,7 +351,7 @@ int fft_configure(nbldpc_code* c) {
   if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
   Plan pl{};
   pl.fpb = 1;
-  pl.threads = kThreads;
+  pl.threads = threads;
   pl.blob_cap = (int)round_up((size_t)c->off.bytes, 16);
   pl.n_cap = (int)round_up((size_t)c->n, 16);
   pl.slot_smem = pl.smem = pl.blob_cap + pl.n_cap + 16;
