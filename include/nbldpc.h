@@ -244,8 +244,9 @@ int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
  * rounding) is set to 0; a normalization whose sum is not positive gives the
  * uniform vector 1/q.
  *
- * Supported codes: check degree <= 8 and column degree <= 8 (the FFT-SPA
- * kernels keep a check's transformed messages in registers); other codes
+ * Supported codes: column degree <= 8, and check degree <= 32 for q <= 64
+ * (one lane per edge) or <= 8 for q = 128, 256 (a check's transformed
+ * messages are spread over the registers of a lane group); other codes
  * return NBLDPC_ERR_UNSUPPORTED from both calls.
  */
 

@@ -11,24 +11,30 @@
 
 namespace nbldpc {
 
-// Address of the FFT-SPA kernel for check degrees <= dc (4 or 8) and column
-// degrees <= dv (2, 4 or 8) of this unit's field order, and its block size;
-// null otherwise.
+// Address of the FFT-SPA kernel of this unit's field order for column degrees
+// <= dv (2, 4 or 8) and check degrees <= dc (4 or 8: distributed check-node
+// pass, q >= 64), or dc = 0 (lane-per-edge check-node pass, q <= 64, check
+// degree <= 32), and its block size; null when there is none.
+template <int DC, int DV> const void* fft_entry(int* threads) {
+  if (threads) *threads = FftThreads<NBLDPC_FQ, DC, DV>::v;
+  return reinterpret_cast<const void*>(&fftspa_decode_kernel<NBLDPC_FQ, DC, DV>);
+}
+
+template <int DC> const void* fft_entry_dv(int dv, int* threads) {
+  if (dv == 2) return fft_entry<DC, 2>(threads);
+  if (dv == 4) return fft_entry<DC, 4>(threads);
+  if (dv == 8) return fft_entry<DC, 8>(threads);
+  return nullptr;
+}
+
 const void* NBLDPC_CAT(fft_kernel_q, NBLDPC_FQ)(int dc, int dv, int* threads) {
-  constexpr int q = NBLDPC_FQ;
-  if (threads) {
-    *threads = dc == 4 ? (dv == 2 ? FftThreads<q, 4, 2>::v : dv == 4 ? FftThreads<q, 4, 4>::v : FftThreads<q, 4, 8>::v)
-                       : (dv == 2 ? FftThreads<q, 8, 2>::v : dv == 4 ? FftThreads<q, 8, 4>::v : FftThreads<q, 8, 8>::v);
-  }
-  if (dc == 4) {
-    if (dv == 2) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 4, 2>);
-    if (dv == 4) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 4, 4>);
-    if (dv == 8) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 4, 8>);
-  } else if (dc == 8) {
-    if (dv == 2) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 8, 2>);
-    if (dv == 4) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 8, 4>);
-    if (dv == 8) return reinterpret_cast<const void*>(&fftspa_decode_kernel<q, 8, 8>);
-  }
+#if NBLDPC_FQ <= 64
+  if (dc == 0) return fft_entry_dv<0>(dv, threads);
+#endif
+#if NBLDPC_FQ >= 64
+  if (dc == 4) return fft_entry_dv<4>(dv, threads);
+  if (dc == 8) return fft_entry_dv<8>(dv, threads);
+#endif
   return nullptr;
 }
 

@@ -37,6 +37,7 @@ struct FftJob {
   uint8_t* out_ok;            // [frames]
   float* out_app;             // [frames][n][q] normalized a-posteriori vectors, or null
   int q, n, m, frames, max_iters, early_stop;
+  int ntasks;                 // warp tasks of the q <= 64 check-node pass (blob task_c0)
 };
 
 struct FftParams {
@@ -44,11 +45,14 @@ struct FftParams {
   unsigned int* counter;      // next frame
   float* msg;                 // message slots, one per block: [nnz][q] floats
   size_t slot_floats;
-  int blob_cap, n_cap;        // shared-memory layout: blob, decisions, control word
+  int blob_cap, n_cap;        // shared-memory layout: blob, decisions, control word,
+  int w_off;                  // then (q <= 64, 256-byte aligned) the transformed vectors, 32 * q floats per warp
 };
 
 template <int Q_> struct FftGeo {
   static constexpr int Q = Q_;
+  static constexpr int LQ = ilog2(Q);                 // p
+  static constexpr int PB = LQ > 0 ? LQ : 1;          // basis images per coefficient
   static constexpr int R = Q < 8 ? Q : 8;             // check-vector elements per lane
   static constexpr int RB = ilog2(R);
   static constexpr int G = Q / R;                     // lanes per check vector (1..32)
@@ -150,11 +154,76 @@ __device__ __forceinline__ void normalize_vec(float (&z)[g::RV], unsigned vmask)
   }
 }
 
+
+// ---------------------------------------------------------------- q <= 64: one lane per edge
+// The lane-per-edge check-node pass (q <= 64) keeps a whole message vector in one lane's
+// registers, so both transforms run without shuffles, and applies the
+// coefficient permutations in the transform domain.  With M_c the GF(2)-linear
+// map "multiply by c" (column k = c x^k), the transform of a permuted vector
+// is the permuted transform:
+//     WHT(u o M_c^-1)(s) = WHT(u)(M_c^T s),
+// so with W_j = WHT(u_j) (natural order) the check node's output is
+//     v'_n = WHT^-1(P_n),  P_n(s) = prod over j != n of W_j(M_{h_j / h_n}^T s).
+// M_c^T s is the XOR of the basis images M_c^T e_i over the bits i of s
+// (at_log[log c][i]); walking s in Gray-code order updates the index with one
+// XOR per element.  W_j sits in shared memory (one 256-byte row per lane for
+// q = 64, 16-byte chunks XOR-swizzled by the lane against bank conflicts),
+// the message rows in global memory are read and written whole.
+__host__ __device__ constexpr int ctz_c(int k) {
+  int b = 0;
+  while (k > 1 && !(k & 1)) { k >>= 1; ++b; }
+  return b;
+}
+
+// all p butterfly stages in registers
+template <int Q> __device__ __forceinline__ void wht_full(float (&v)[Q]) {
+#pragma unroll
+  for (int h = 1; h < Q; h <<= 1) {
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      if (!(r & h)) {
+        const float a = v[r], b = v[r + h];
+        v[r] = a + b;
+        v[r + h] = a - b;
+      }
+    }
+  }
+}
+
+// 16-byte-chunk swizzle of a lane's row (element positions XOR swz)
+template <int Q> __device__ __forceinline__ int row_swz(int lane) {
+  if constexpr (Q >= 8) return (lane & (Q / 4 - 1)) << 2;
+  else return 0;
+}
+
+// The block's dynamic shared memory (code blob, decisions, control word,
+// transformed vectors), addressed by byte offset.
+extern __shared__ __align__(16) unsigned char fft_smem[];
+
+// acc[s] (=|*=) row[(M s) ^ swz] for s = 0..Q-1 in Gray-code order: step K
+// visits s = K ^ (K >> 1), which differs from the previous s in bit ctz(K),
+// so the element's byte offset changes by XOR with a4[ctz(K)] = 4 M e_ctz(K).
+// `cur` starts at the row's byte offset XOR 4 swz (rows are aligned to their
+// length, so XOR within the row is addition).
+template <int Q, bool FIRST, int K = 0>
+__device__ __forceinline__ void gray_gather(float (&acc)[Q], const int (&a4)[ilog2(Q) > 0 ? ilog2(Q) : 1], int cur) {
+  if constexpr (K > 0) {
+    constexpr int b = ctz_c(K);
+    cur ^= a4[b];
+  }
+  constexpr int sk = K ^ (K >> 1);
+  const float x = *reinterpret_cast<const float*>(fft_smem + cur);
+  if constexpr (FIRST) acc[sk] = x; else acc[sk] *= x;
+  if constexpr (K + 1 < Q) gray_gather<Q, FIRST, K + 1>(acc, a4, cur);
+}
+
 // ---------------------------------------------------------------- one frame
-// DC >= every check degree, DV >= every column degree (register arrays).
+// DC >= every check degree (register arrays of the distributed check-node
+// pass), or DC = 0: the lane-per-edge check-node pass (q <= 64, check degree
+// <= 32); DV >= every column degree.
 template <class g, int DC, int DV>
 __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, float* X, const unsigned char* sblob,
-                                                 uint8_t* chat) {
+                                                 uint8_t* chat, float* wsm) {
   constexpr int Q = g::Q, R = g::R, RV = g::RV;
   const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
   const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
@@ -164,6 +233,9 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
   const uint8_t* edge_lhi = sblob + job.off.edge_lhi;  // log_x(h^-1) of each edge
   const uint16_t* vn_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_ptr);
   const uint16_t* vn_edge = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_edge);
+  const uint16_t* edge_row = reinterpret_cast<const uint16_t*>(sblob + job.off.edge_row);
+  const uint16_t* task_c0 = reinterpret_cast<const uint16_t*>(sblob + job.off.task_c0);
+  const uint8_t* at_log = sblob + job.off.at_log;
 
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   const int grp = tid / g::G, ngroups = nthr / g::G, gl = tid % g::G;
@@ -249,9 +321,73 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
     return __syncthreads_or(bad) == 0;
   };
 
+
+  // ---- check-node pass for q <= 64 (Alg. 1: permutation, FFT, product,
+  // inverse FFT, depermutation), one lane per edge, warp tasks of whole checks
+  auto cnp_lane = [&](bool first) {
+    if constexpr (DC == 0 && Q <= 64) {
+    constexpr int P = g::PB;
+    const int warp = tid >> 5, nwarps = nthr >> 5;
+    const int w_row0 = (int)(reinterpret_cast<unsigned char*>(wsm) - fft_smem);   // byte offset, 256-aligned
+    float* wrow = wsm + ((size_t)warp * 32 + lane) * Q;        // this lane's transformed vector
+    const int swz = row_swz<Q>(lane);
+    for (int t = warp; t < job.ntasks; t += nwarps) {
+      const int eb = row_ptr[task_c0[t]], ee = row_ptr[task_c0[t + 1]];
+      const int e = eb + lane;
+      const bool valid = e < ee;
+      if (valid) {
+        float v[Q];
+        load_vec<Q>(first ? pf + (size_t)edge_col[e] * Q : X + (size_t)e * Q, v);   // u^(0) = p
+        wht_full<Q>(v);                                                            // W_e = FFT(u_e)
+        if constexpr (Q >= 4) {
+#pragma unroll
+          for (int c = 0; c < Q / 4; ++c)
+            reinterpret_cast<float4*>(wrow)[c ^ (swz >> 2)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) wrow[i] = v[i];
+        }
+      }
+      __syncwarp();
+      if (valid) {
+        const int r = edge_row[e], e0 = row_ptr[r], d = row_ptr[r + 1] - e0, n = e - e0;
+        const int lhn = edge_lh[e];
+        // basis images (byte offsets) of M^T for c = h_j / h_n, and the start offset of lane j's row
+        auto setup = [&](int j, int (&a4)[P]) {
+          int lc = edge_lh[e0 + j] - lhn;
+          if (lc < 0) lc += Q - 1;
+#pragma unroll
+          for (int b = 0; b < P; ++b) a4[b] = 4 * at_log[lc * g::LQ + b];
+          const int lj = lane - n + j;
+          return (w_row0 + (warp * 32 + lj) * Q * 4) ^ (4 * row_swz<Q>(lj));
+        };
+        float acc[Q];
+        const int jfirst = n == 0 ? 1 : 0;
+        {
+          int a4[P];
+          const int cur = setup(jfirst, a4);
+          gray_gather<Q, true>(acc, a4, cur);
+        }
+        for (int j = jfirst + 1; j < d; ++j) {
+          if (j == n) continue;
+          int a4[P];
+          const int cur = setup(j, a4);
+          gray_gather<Q, false>(acc, a4, cur);
+        }
+        wht_full<Q>(acc);                                                          // inverse FFT (times q)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] = fmaxf(acc[i] * (1.f / Q), 0.f);       // v'_e, rounding below 0 -> 0
+        store_vec<Q>(X + (size_t)e * Q, acc);
+      }
+      __syncwarp();
+    }
+    }
+  };
+
   // ---- check-node pass (Alg. 1: permutation, FFT, product, inverse FFT,
   // depermutation), one group of G lanes per check
   auto cnp = [&](bool first) {
+    if constexpr (DC > 0) {
     for (int r = grp; r < job.m; r += ngroups) {
       const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
       float W[DC][R];
@@ -294,6 +430,7 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
         }
       }
     }
+    }
   };
 
   // ---- decode one frame
@@ -303,7 +440,7 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
   int iters = 0;
   if (!(job.early_stop && ok)) {
     for (int k = 1; k <= job.max_iters; ++k) {
-      cnp(k == 1);
+      if constexpr (DC == 0) cnp_lane(k == 1); else cnp(k == 1);
       __syncthreads();
       vnp(false, k < job.max_iters);
       __syncthreads();
@@ -321,31 +458,33 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
 
 // ---------------------------------------------------------------- the kernel
 // Threads of one block: one frame per SM, as many warps as the register
-// arrays allow (80 registers per thread: 24 warps; 128: 16 warps).  A single
+// arrays allow (80 registers per thread: 24 warps; 128: 16 warps; q = 64
+// holds two 64-float vectors per lane).  A single
 // frame's message slot per SM (nnz * q floats, 295 KB for GF(64) N=576) keeps
 // the resident message state of the whole GPU inside L2.
 template <int Q, int DC, int DV> struct FftThreads {
-  static constexpr int v = (DC <= 4 && Q < 256) ? 768 : 512;
+  static constexpr int v = DC == 0 ? (Q == 64 ? 512 : 768) : ((DC <= 4 && Q < 256) ? 768 : 512);
 };
 
 // Persistent blocks, one frame at a time; DC / DV bound the check and column
 // degrees of the code (register arrays of the two passes).
 template <int Q, int DC, int DV>
 __global__ void __launch_bounds__(FftThreads<Q, DC, DV>::v, 1) fftspa_decode_kernel(const __grid_constant__ FftParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* smem = fft_smem;
   unsigned char* sblob = smem;
   uint8_t* chat = smem + p.blob_cap;
   volatile int* ctl = reinterpret_cast<volatile int*>(smem + p.blob_cap + p.n_cap);
   const FftJob& job = p.job;
   float* X = p.msg + (size_t)blockIdx.x * p.slot_floats;
-  for (int i = threadIdx.x; i < job.off.bytes / 16; i += blockDim.x)
+  float* wsm = reinterpret_cast<float*>(smem + p.w_off);
+  for (int i = threadIdx.x; i < job.off.fft_bytes / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(sblob)[i] = reinterpret_cast<const uint4*>(job.blob)[i];
   for (;;) {
     if (threadIdx.x == 0) ctl[0] = (int)atomicAdd(p.counter, 1u);
     __syncthreads();
     const int frame = ctl[0];
     if (frame >= job.frames) break;
-    fft_decode_frame<FftGeo<Q>, DC, DV>(job, frame, X, sblob, chat);
+    fft_decode_frame<FftGeo<Q>, DC, DV>(job, frame, X, sblob, chat, wsm);
     __syncthreads();
   }
 }

@@ -213,6 +213,9 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
 // ---------------------------------------------------------------- parameters
 struct CodeBlob {           // offsets (bytes) into the code blob
   int exp2, log, row_ptr, edge_col, edge_lh, edge_lhi, vn_ptr, vn_edge, bytes;
+  // FFT-SPA section, after `bytes` (the min-max kernels stage only [0, bytes)):
+  // check of each edge, first check of each warp task, transposed-multiplication basis
+  int edge_row, task_c0, at_log, fft_bytes;
 };
 
 // One code and the frames to decode with it.

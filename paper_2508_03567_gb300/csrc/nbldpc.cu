@@ -46,7 +46,8 @@ struct nbldpc_code {
   int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
   Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
   int fft_status = NBLDPC_ERR_UNSUPPORTED;   // FFT-SPA launch shape below valid when NBLDPC_OK
-  int fft_dc = 0, fft_dv = 0;          // degree buckets of the FFT-SPA kernel
+  int fft_dc = 0, fft_dv = 0;          // degree buckets of the FFT-SPA kernel (dc 0: q <= 64 lane-per-edge path)
+  int ntasks = 0;                      // FFT-SPA warp tasks (blob section)
   Plan fft_plan{};
   std::mutex mu;                       // guards the lazily created copy stream
   cudaStream_t side = nullptr;         // second stream for nbldpc_decode_host
@@ -330,16 +331,21 @@ const void* fft_kernel_for(int q, int dc, int dv, int* threads = nullptr) {
   return nullptr;
 }
 
-bool g_fft_attr_done[64][8][2][3] = {};   // device, log2(q) - 1, check-degree bucket, column-degree bucket
+bool g_fft_attr_done[64][8][3][3] = {};   // device, log2(q) - 1, check-node form, column-degree bucket
 
 // Launch shape of the FFT-SPA kernel for a code: degree buckets (check
 // degree <= 4 or 8, column degree <= 2, 4 or 8), block size (one frame per
 // SM), shared memory (code blob, decisions, control word), resident blocks,
 // message slot of nnz * q floats.
 int fft_configure(nbldpc_code* c) {
-  const int dc = c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : 0);
+  // check-node form: lane per edge (dc 0: check degree <= 32) for q <= 32,
+  // and for q = 64 codes with a check of degree > 8; otherwise the
+  // distributed form with the check degree bucket 4 or 8 (measured on GB300:
+  // GF(16) 1.43 vs 1.29 Gbit/s lane per edge, GF(64) 0.88 vs 0.66 distributed)
+  const bool lane_form = c->q <= 32 || (c->q == 64 && c->dmax > 8);
+  const int dc = lane_form ? (c->dmax <= 32 ? 0 : -1) : (c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : -1));
   const int dv = c->vmax <= 2 ? 2 : (c->vmax <= 4 ? 4 : (c->vmax <= 8 ? 8 : 0));
-  if (!dc || !dv) return NBLDPC_ERR_UNSUPPORTED;
+  if (dc < 0 || !dv) return NBLDPC_ERR_UNSUPPORTED;
   int threads = 0;
   const void* k = fft_kernel_for(c->q, dc, dv, &threads);
   if (!k) return NBLDPC_ERR_UNSUPPORTED;
@@ -352,13 +358,14 @@ int fft_configure(nbldpc_code* c) {
   Plan pl{};
   pl.fpb = 1;
   pl.threads = threads;
-  pl.blob_cap = (int)round_up((size_t)c->off.bytes, 16);
+  pl.blob_cap = (int)round_up((size_t)c->off.fft_bytes, 16);
   pl.n_cap = (int)round_up((size_t)c->n, 16);
-  pl.slot_smem = pl.smem = pl.blob_cap + pl.n_cap + 16;
+  const int w_area = dc == 0 ? threads * c->q * (int)sizeof(float) : 0;   // one transformed vector per lane
+  pl.slot_smem = pl.smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16), 256) + w_area;
   if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
   {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    bool& done = g_fft_attr_done[dev][nbldpc::ilog2(c->q) - 1][dc == 8][dv == 2 ? 0 : (dv == 4 ? 1 : 2)];
+    bool& done = g_fft_attr_done[dev][nbldpc::ilog2(c->q) - 1][dc == 0 ? 0 : (dc == 4 ? 1 : 2)][dv == 2 ? 0 : (dv == 4 ? 1 : 2)];
     if (!done) {
       if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
         return NBLDPC_ERR_CUDA;
@@ -398,6 +405,8 @@ int fft_launch(const nbldpc_code* c, const float* prob, int frames, int max_iter
   fp.slot_floats = pl.slot_bytes / sizeof(float);
   fp.blob_cap = pl.blob_cap;
   fp.n_cap = pl.n_cap;
+  fp.w_off = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16), 256);
+  fp.job.ntasks = c->ntasks;
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
   void* args[] = {&fp};
@@ -527,7 +536,35 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   off.vn_ptr = take(2 * ((size_t)n_cols + 1));
   off.vn_edge = take(2 * (size_t)nnz);
   off.bytes = (int)o;
+  // FFT-SPA section: warp tasks pack consecutive checks with at most 32 edges in all
+  std::vector<uint16_t> tasks;
+  for (int r = 0; r < n_rows;) {
+    tasks.push_back((uint16_t)r);
+    int edges = 0;
+    while (r < n_rows && edges + (row_ptr[r + 1] - row_ptr[r]) <= 32) edges += row_ptr[r + 1] - row_ptr[r], ++r;
+    if (edges == 0) ++r;   // a check of degree > 32: its own task (such codes are rejected for q <= 64)
+  }
+  tasks.push_back((uint16_t)n_rows);
+  const int pbits = [&] { int b = 0; while ((1 << b) < q) ++b; return b; }();
+  off.edge_row = take(2 * (size_t)nnz);
+  off.task_c0 = take(2 * tasks.size());
+  off.at_log = take((size_t)(q - 1) * pbits);
+  off.fft_bytes = (int)o;
   std::vector<unsigned char> blob(o, 0);
+  {
+    uint16_t* er = reinterpret_cast<uint16_t*>(&blob[off.edge_row]);
+    for (int r = 0; r < n_rows; ++r)
+      for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) er[e] = (uint16_t)r;
+    memcpy(&blob[off.task_c0], tasks.data(), 2 * tasks.size());
+    // at_log[lc][i] = M_c^T e_i for c = x^lc: bit k is bit i of c x^k
+    uint8_t* at = &blob[off.at_log];
+    for (int lc = 0; lc < q - 1; ++lc)
+      for (int i = 0; i < pbits; ++i) {
+        int a = 0;
+        for (int k = 0; k < pbits; ++k) a |= ((exp2[lc + k] >> i) & 1) << k;
+        at[lc * pbits + i] = (uint8_t)a;
+      }
+  }
   memcpy(&blob[off.exp2], exp2.data(), 2 * (size_t)q);
   memcpy(&blob[off.log], lg.data(), (size_t)q);
   uint16_t* rp = reinterpret_cast<uint16_t*>(&blob[off.row_ptr]);
@@ -560,6 +597,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   c->nnz = nnz;
   c->dmax = dmax;
   c->vmax = vmax;
+  c->ntasks = (int)tasks.size() - 1;
   c->poly = prim_poly;
   c->off = off;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return NBLDPC_ERR_CUDA; }

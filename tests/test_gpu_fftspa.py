@@ -52,10 +52,10 @@ def assert_decisions(code, got, want, app_want, what):
 def irregular_code(q, seed, dmax=8):
     """Rows of degree 2..dmax, columns of degree >= 1, random coefficients (degrees stay within the limits)."""
     rng = np.random.default_rng(seed)
-    n, m = 70, 30
+    n, m = (70, 30) if dmax <= 8 else (260, 30)
     h = np.zeros((m, n), np.int64)
     for r in range(m):
-        d = int(rng.integers(2, dmax))
+        d = int(rng.integers(2, dmax + 1))
         cols = rng.choice(n, d, replace=False)
         h[r, cols] = rng.integers(1, q, d)
     for c in range(n):
@@ -114,9 +114,10 @@ def test_decisions_match_the_oracle(name, shape, eb, frames):
             assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("q", [4, 16, 64, 256])
-def test_irregular_code(q):
-    code = irregular_code(q, q)
+@pytest.mark.parametrize("q,dmax", [(4, 8), (16, 8), (64, 8), (256, 8), (2, 20), (8, 32), (32, 20), (64, 24)])
+def test_irregular_code(q, dmax):
+    """Check degrees up to 32 for q <= 64 (lane per edge), up to 8 for q = 256."""
+    code = irregular_code(q, q + dmax, dmax)
     rng = np.random.default_rng(q + 1)
     w = rng.random((16, code.n, q)) ** 4
     hard = rng.integers(0, q, (16, code.n))
@@ -196,17 +197,19 @@ def test_arguments_are_checked():
     with pytest.raises(binding.NbldpcError) as ei:        # negative iteration count
         binding.nbldpc_fftspa_decode(dec.handle, p, 4, -1, 1, sym, its, ok, None, ws)
     assert ei.value.status == binding.NBLDPC_ERR_ARG
-    # check degree 9: outside the kernels' limits
-    rng = np.random.default_rng(1)
-    h = np.zeros((4, 20), np.int64)
-    h[0, :9] = rng.integers(1, 4, 9)
-    for r in range(1, 4):
-        h[r, 9 + 3 * (r - 1): 9 + 3 * r + 2] = rng.integers(1, 4, 5)
-    h[1:, 19] = 1
-    big = binding.Decoder.from_code(I.code_from_dense(h, 4, I.PRIMITIVE_POLY[4]))
-    with pytest.raises(binding.NbldpcError) as ei:
-        binding.nbldpc_fftspa_workspace_size(big.handle, 4)
-    assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
+    # check degree 9 at q = 256 and 33 at q = 4: outside the kernels' limits
+    for q, deg in ((256, 9), (4, 33)):
+        rng = np.random.default_rng(q)
+        n = deg + 12
+        h = np.zeros((4, n), np.int64)
+        h[0, :deg] = rng.integers(1, q, deg)
+        for r in range(1, 4):
+            h[r, deg + 4 * (r - 1): deg + 4 * r] = rng.integers(1, q, 4)
+        h[1:, 0] = 1
+        big = binding.Decoder.from_code(I.code_from_dense(h, q, I.PRIMITIVE_POLY[q]))
+        with pytest.raises(binding.NbldpcError) as ei:
+            binding.nbldpc_fftspa_workspace_size(big.handle, 4)
+        assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
 
 
 def test_full_size_sampled():
