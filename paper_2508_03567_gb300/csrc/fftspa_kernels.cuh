@@ -56,8 +56,16 @@ template <int Q_> struct FftGeo {
   static constexpr int R = Q < 8 ? Q : 8;             // check-vector elements per lane
   static constexpr int RB = ilog2(R);
   static constexpr int G = Q / R;                     // lanes per check vector (1..32)
-  static constexpr int RV = Q <= 4 ? Q : (Q / 32 > 4 ? Q / 32 : 4);   // variable-vector elements per lane
-  static constexpr int VG = Q / RV;                   // lanes per variable vector (1..32)
+};
+
+// Variable-node lanes: RV elements of a vector per lane, VG lanes per vector
+// (1..32).  8-element lanes for q >= 64 shorten the shuffle reductions
+// (decision, normalization) by one stage where the column degree leaves the
+// registers for them.
+template <int Q, int DV> struct VnpGeo {
+  static constexpr int Q_ = Q;
+  static constexpr int RV = Q <= 4 ? Q : ((Q >= 64 && DV <= 4) ? 8 : (Q / 32 > 4 ? Q / 32 : 4));
+  static constexpr int VG = Q / RV;
 };
 
 // Walsh-Hadamard butterflies over the R register elements (index bits
@@ -134,6 +142,7 @@ template <int N> __device__ __forceinline__ void store_vec(float* p, const float
 // tree adds the same pairs on every lane, in commuted order).
 template <class g>
 __device__ __forceinline__ void normalize_vec(float (&z)[g::RV], unsigned vmask) {
+  static_assert(g::Q_ >= 2, "variable-node geometry");
   float s = 0.f;
 #pragma unroll
   for (int r = 0; r < g::RV; ++r) s += z[r];
@@ -150,7 +159,7 @@ __device__ __forceinline__ void normalize_vec(float (&z)[g::RV], unsigned vmask)
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < g::RV; ++r) z[r] = 1.f / g::Q;
+    for (int r = 0; r < g::RV; ++r) z[r] = 1.f / g::Q_;
   }
 }
 
@@ -224,7 +233,8 @@ __device__ __forceinline__ void gray_gather(float (&acc)[Q], const int (&a4)[ilo
 template <class g, int DC, int DV>
 __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, float* X, const unsigned char* sblob,
                                                  uint8_t* chat, float* wsm) {
-  constexpr int Q = g::Q, R = g::R, RV = g::RV;
+  using vg = VnpGeo<g::Q, DV>;
+  constexpr int Q = g::Q, R = g::R, RV = vg::RV;
   const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
   const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
   const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.row_ptr);
@@ -243,8 +253,8 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
   const int y0 = gl * R;
   const bool y0nz = y0 != 0;
   const int ly0 = y0nz ? glog[y0] : 0;
-  const int vgrp = tid / g::VG, nvgroups = nthr / g::VG, vgl = tid % g::VG;
-  const unsigned vmask = group_mask<g::VG>(lane);
+  const int vgrp = tid / vg::VG, nvgroups = nthr / vg::VG, vgl = tid % vg::VG;
+  const unsigned vmask = group_mask<vg::VG>(lane);
   const float* pf = job.prob + (size_t)frame * job.n * Q;
   float* app = job.out_app ? job.out_app + (size_t)frame * job.n * Q : nullptr;
 
@@ -276,14 +286,14 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
       for (int r = 1; r < RV; ++r)
         if (T[r] > bv) { bv = T[r]; bi = vgl * RV + r; }
 #pragma unroll
-      for (int o = 1; o < g::VG; o <<= 1) {
+      for (int o = 1; o < vg::VG; o <<= 1) {
         const float ov = __shfl_xor_sync(vmask, bv, o);
         const int oi = __shfl_xor_sync(vmask, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
       }
       if (vgl == 0) chat[vn] = (uint8_t)bi;
       if (app) {
-        normalize_vec<g>(T, vmask);
+        normalize_vec<vg>(T, vmask);
         store_vec<RV>(app + (size_t)vn * Q + vgl * RV, T);
       }
       if (!first && want_u) {
@@ -299,7 +309,7 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
                 if (b != a) t *= V[b][r];
               z[r] = t;
             }
-            normalize_vec<g>(z, vmask);
+            normalize_vec<vg>(z, vmask);
             store_vec<RV>(X + (size_t)vn_edge[k0 + a] * Q + vgl * RV, z);
           }
         }
