@@ -79,23 +79,22 @@ def dist_setup(args):
     return ws, rank, local
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(source: str = "mma_kernels.cuh") -> str:
     h = hashlib.sha256()
-    for f in ("mma_kernels.cuh",):
-        with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", source), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(per_frame_iter_pairs):
-    """DRAM bytes per launch from the committed ncu summary, if it is current."""
-    path = os.path.join(ROOT, "profiles", "mma_decode_kernel_gf64_n576.md")
+def profiled_traffic(profile: str = "mma_decode_kernel_gf64_n576.md", source: str = "mma_kernels.cuh"):
+    """DRAM bytes per frame from a committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None, None
     txt = open(path).read()
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m_bpf = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", txt)
-    if not m_hash or not m_bpf or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bpf or m_hash.group(1) != kernel_source_hash(source):
         return None, path
     return float(m_bpf.group(1)), path
 
@@ -569,6 +568,7 @@ def run_fftspa(args, ws, rank, local):
     mhz, mhz_kind = sm_max_mhz()
     peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / 1e9
     info_bits = frames * code.k * code.p
+    fbpf, _ = profiled_traffic("fftspa_decode_kernel_gf64_n576.md", "fftspa_kernels.cuh")
 
     # end to end: pinned host probabilities in chunks, copies and decode on one stream, outputs back
     e2e = None
@@ -627,7 +627,7 @@ def run_fftspa(args, ws, rank, local):
                    "max_iters": mi, "early_stop": bool(es), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"frames sharded over {ws} GPU(s)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": None if fbpf is None else fbpf * frames,
                      "peak_kind": f"derived: 152 SMs x 128 fp32 lanes x {mhz:.0f} MHz ({mhz_kind} max SM clock), "
                                   "one add or multiply per lane per clock"},
         "clocks": clk.summary(),
@@ -722,7 +722,7 @@ def main():
     clocks = clk.summary()
     mhz, mhz_kind = sm_max_mhz()
     peak_gops = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
-    bpf, _ = profiled_traffic(pairs_fi)
+    bpf, _ = profiled_traffic()
 
     e2e = None
     if not args.no_e2e:
