@@ -286,6 +286,27 @@ int nbldpc_fftspa_decode(const nbldpc_code *code, const float *prob_dev, int fra
                          int early_stop, uint8_t *out_sym_dev, int32_t *out_iters_dev, uint8_t *out_ok_dev,
                          float *out_app_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
+/* Device workspace nbldpc_fftspa_decode_host needs for chunks of
+ * `chunk_frames` frames, in bytes (two chunks of probabilities, outputs and
+ * decoder workspace). */
+int nbldpc_fftspa_decode_host_workspace_size(const nbldpc_code *code, int chunk_frames, size_t *bytes);
+
+/*
+ * nbldpc_fftspa_decode on HOST buffers: prob_host [frames][n_cols][q] float
+ * (pinned memory lets the copies overlap), outputs out_sym_host
+ * [frames][n_cols] uint8, out_iters_host [frames] int32, out_ok_host [frames]
+ * uint8.  Frames move in chunks of `chunk_frames`: one chunk's host-to-device
+ * copy, decode and device-to-host copies are queued on one of two streams (the
+ * caller's stream and a stream owned by the code handle) so that copies and
+ * decoding of consecutive chunks overlap, as in nbldpc_decode_host.
+ * workspace_dev: device, >= nbldpc_fftspa_decode_host_workspace_size bytes,
+ * 256-byte aligned.  Returns after queueing; the outputs are valid once
+ * `cuda_stream` has completed.  One host decode at a time per handle.
+ */
+int nbldpc_fftspa_decode_host(const nbldpc_code *code, const float *prob_host, int frames, int max_iters,
+                              int early_stop, uint8_t *out_sym_host, int32_t *out_iters_host, uint8_t *out_ok_host,
+                              int chunk_frames, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
 /*
  * Size of the fixed device array that nbldpc_decode_noalloc works in.
  */

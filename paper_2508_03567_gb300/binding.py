@@ -32,6 +32,7 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
             "nbldpc_code_autotune", "nbldpc_code_set_message_bits", "nbldpc_code_get_message_bits",
             "nbldpc_fftspa_workspace_size", "nbldpc_fftspa_decode",
+            "nbldpc_fftspa_decode_host_workspace_size", "nbldpc_fftspa_decode_host",
             "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
@@ -93,6 +94,9 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_fftspa_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_fftspa_decode.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                                vp, sz, vp]
+            L.nbldpc_fftspa_decode_host_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
+            L.nbldpc_fftspa_decode_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                                    ctypes.c_int, vp, sz, vp]
             L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]
@@ -199,6 +203,26 @@ def nbldpc_fftspa_decode(handle: int, prob, frames: int, max_iters: int, early_s
                                     _ptr(out_sym), _ptr(out_iters), _ptr(out_ok), _ptr(out_app),
                                     _ptr(workspace), int(workspace_bytes), _stream_ptr(stream))
     _check(st, "nbldpc_fftspa_decode")
+
+
+def nbldpc_fftspa_decode_host_workspace_size(handle: int, chunk_frames: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nbldpc_fftspa_decode_host_workspace_size(handle, int(chunk_frames), ctypes.byref(b)),
+           "nbldpc_fftspa_decode_host_workspace_size")
+    return b.value
+
+
+def nbldpc_fftspa_decode_host(handle: int, prob_host, frames: int, max_iters: int, early_stop: int,
+                              out_sym_host, out_iters_host, out_ok_host, chunk_frames: int, workspace,
+                              workspace_bytes: int | None = None, stream=None) -> None:
+    """Queue an FFT-SPA decode of host buffers (pinned for overlap); sync `stream` before reading outputs."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size()
+    st = lib().nbldpc_fftspa_decode_host(handle, _ptr(prob_host), int(frames), int(max_iters), int(early_stop),
+                                         _ptr(out_sym_host), _ptr(out_iters_host), _ptr(out_ok_host),
+                                         int(chunk_frames), _ptr(workspace), int(workspace_bytes),
+                                         _stream_ptr(stream))
+    _check(st, "nbldpc_fftspa_decode_host")
 
 
 def nbldpc_decode_host(handle: int, gamma_host, frames: int, max_iters: int, early_stop: int,

@@ -13,8 +13,8 @@ namespace nbldpc {
 
 // Address of the FFT-SPA kernel of this unit's field order for column degrees
 // <= dv (2, 4 or 8) and check degrees <= dc (4 or 8: distributed check-node
-// pass, q >= 64), or dc = 0 (lane-per-edge check-node pass, q <= 64, check
-// degree <= 32), and its block size; null when there is none.
+// pass), or dc = 0 (lane-per-edge check-node pass, q <= 64, check degree
+// <= 32), and its block size; null when there is none.
 template <int DC, int DV> const void* fft_entry(int* threads) {
   if (threads) *threads = FftThreads<NBLDPC_FQ, DC, DV>::v;
   return reinterpret_cast<const void*>(&fftspa_decode_kernel<NBLDPC_FQ, DC, DV>);
@@ -31,10 +31,8 @@ const void* NBLDPC_CAT(fft_kernel_q, NBLDPC_FQ)(int dc, int dv, int* threads) {
 #if NBLDPC_FQ <= 64
   if (dc == 0) return fft_entry_dv<0>(dv, threads);
 #endif
-#if NBLDPC_FQ >= 64
   if (dc == 4) return fft_entry_dv<4>(dv, threads);
   if (dc == 8) return fft_entry_dv<8>(dv, threads);
-#endif
   return nullptr;
 }
 

@@ -49,22 +49,33 @@ struct FftParams {
   int w_off;                  // then (q <= 64, 256-byte aligned) the transformed vectors, 32 * q floats per warp
 };
 
+// Elements per lane and block size of the distributed check-node form at
+// q = 64 (compile-time tuning knobs; the defaults are the measured best on
+// GB300, GF(64) (2,4) N=576: 4 elements / 768 threads 1.19 Gbit/s, 8 / 768
+// 0.97, 16 / 512 0.72, 2 / 1024 1.05, 4 / 896 1.08).
+#ifndef NBLDPC_FFT_R64
+#define NBLDPC_FFT_R64 4
+#endif
+#ifndef NBLDPC_FFT_T64
+#define NBLDPC_FFT_T64 768
+#endif
+
 template <int Q_> struct FftGeo {
   static constexpr int Q = Q_;
   static constexpr int LQ = ilog2(Q);                 // p
   static constexpr int PB = LQ > 0 ? LQ : 1;          // basis images per coefficient
-  static constexpr int R = Q < 8 ? Q : 8;             // check-vector elements per lane
+  static constexpr int R = Q < 8 ? (Q < 4 ? Q : 4) : (Q <= 64 ? NBLDPC_FFT_R64 : 8);   // check-vector elements per lane
   static constexpr int RB = ilog2(R);
   static constexpr int G = Q / R;                     // lanes per check vector (1..32)
 };
 
 // Variable-node lanes: RV elements of a vector per lane, VG lanes per vector
 // (1..32).  8-element lanes for q >= 64 shorten the shuffle reductions
-// (decision, normalization) by one stage where the column degree leaves the
-// registers for them.
+// (decision, normalization) by one stage; column degree 2 only (with 4 the
+// register arrays of the pass no longer fit 80 registers).
 template <int Q, int DV> struct VnpGeo {
   static constexpr int Q_ = Q;
-  static constexpr int RV = Q <= 4 ? Q : ((Q >= 64 && DV <= 4) ? 8 : (Q / 32 > 4 ? Q / 32 : 4));
+  static constexpr int RV = Q <= 4 ? Q : ((Q >= 64 && DV <= 2) ? 8 : (Q / 32 > 4 ? Q / 32 : 4));
   static constexpr int VG = Q / RV;
 };
 
@@ -473,7 +484,8 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
 // frame's message slot per SM (nnz * q floats, 295 KB for GF(64) N=576) keeps
 // the resident message state of the whole GPU inside L2.
 template <int Q, int DC, int DV> struct FftThreads {
-  static constexpr int v = DC == 0 ? (Q == 64 ? 512 : 768) : ((DC <= 4 && Q < 256) ? 768 : 512);
+  static constexpr int v = DC == 0 ? (Q == 64 ? 512 : 768)
+                                   : (Q == 64 ? NBLDPC_FFT_T64 : ((DC <= 4 && Q < 256) ? 768 : 512));
 };
 
 // Persistent blocks, one frame at a time; DC / DV bound the check and column

@@ -331,6 +331,15 @@ const void* fft_kernel_for(int q, int dc, int dv, int* threads = nullptr) {
   return nullptr;
 }
 
+// Largest field order whose codes take the lane-per-edge check-node form at
+// every check degree (compile-time tuning knob).  Measured on GB300 (Mbit/s,
+// lane per edge against distributed with 4 elements per lane): GF(4) (2,4)
+// N=48 1336 vs 1117, GF(8) (2,4) N=512 1441 vs 1467, GF(16) (2,4) N=1024
+// 1432 vs 1759, GF(32) (3,6) N=600 408 vs 588.
+#ifndef NBLDPC_FFT_LANE_MAXQ
+#define NBLDPC_FFT_LANE_MAXQ 4
+#endif
+
 bool g_fft_attr_done[64][8][3][3] = {};   // device, log2(q) - 1, check-node form, column-degree bucket
 
 // Launch shape of the FFT-SPA kernel for a code: degree buckets (check
@@ -338,11 +347,10 @@ bool g_fft_attr_done[64][8][3][3] = {};   // device, log2(q) - 1, check-node for
 // SM), shared memory (code blob, decisions, control word), resident blocks,
 // message slot of nnz * q floats.
 int fft_configure(nbldpc_code* c) {
-  // check-node form: lane per edge (dc 0: check degree <= 32) for q <= 32,
-  // and for q = 64 codes with a check of degree > 8; otherwise the
-  // distributed form with the check degree bucket 4 or 8 (measured on GB300:
-  // GF(16) 1.43 vs 1.29 Gbit/s lane per edge, GF(64) 0.88 vs 0.66 distributed)
-  const bool lane_form = c->q <= 32 || (c->q == 64 && c->dmax > 8);
+  // check-node form: lane per edge (dc 0: check degree <= 32) for small fields
+  // and for q <= 64 codes with a check of degree > 8; otherwise the
+  // distributed form with the check degree bucket 4 or 8
+  const bool lane_form = c->q <= NBLDPC_FFT_LANE_MAXQ || (c->q <= 64 && c->dmax > 8);
   const int dc = lane_form ? (c->dmax <= 32 ? 0 : -1) : (c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : -1));
   const int dv = c->vmax <= 2 ? 2 : (c->vmax <= 4 ? 4 : (c->vmax <= 8 ? 8 : 0));
   if (dc < 0 || !dv) return NBLDPC_ERR_UNSUPPORTED;
@@ -414,6 +422,66 @@ int fft_launch(const nbldpc_code* c, const float* prob, int frames, int max_iter
                        args, (size_t)pl.smem, st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  return NBLDPC_OK;
+}
+
+// ---- host-buffer decodes (nbldpc_decode_host, nbldpc_fftspa_decode_host) ------
+// One chunk's device buffers: input rows, symbols, iterations, ok flags, decoder workspace.
+size_t host_chunk_bytes(const nbldpc_code* c, int chunk_frames, size_t in_bytes_per_frame, size_t decode_ws) {
+  return round_up((size_t)chunk_frames * in_bytes_per_frame, 256) + round_up((size_t)chunk_frames * c->n, 256) +
+         round_up((size_t)chunk_frames * 4, 256) + round_up((size_t)chunk_frames, 256) + round_up(decode_ws, 256);
+}
+
+// Decode host rows in chunks: chunk i copies its rows in, decodes and copies its
+// outputs back on stream i % 2 (the caller's stream or the code's side stream),
+// in buffer half i % 2 of the workspace, so one chunk's copies overlap the other's
+// decode.  `per` is one half's size; `dec` queues the decode of one chunk.
+template <class Dec>
+int host_chunks(nbldpc_code* c, const void* in_host, size_t fbytes, int frames, uint8_t* out_sym_host,
+                int32_t* out_iters_host, uint8_t* out_ok_host, int chunk_frames, void* workspace_dev,
+                size_t workspace_bytes, size_t per, void* cuda_stream, Dec dec) {
+  if (!in_host || !out_sym_host || !out_iters_host || !out_ok_host || !workspace_dev) return NBLDPC_ERR_ARG;
+  if (!aligned(workspace_dev, 256) || workspace_bytes < 2 * per) return NBLDPC_ERR_ARG;
+  int st = cuda_status(cudaGetLastError());
+  if (st != NBLDPC_OK) return st;
+  cudaStream_t main = reinterpret_cast<cudaStream_t>(cuda_stream);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->side) {
+      if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) return NBLDPC_ERR_CUDA;
+      for (auto& ev : c->ev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return NBLDPC_ERR_CUDA;
+    }
+  }
+  std::lock_guard<std::mutex> lk(c->mu);  // one host decode at a time per handle (shared side stream)
+  const size_t g_b = round_up((size_t)chunk_frames * fbytes, 256), s_b = round_up((size_t)chunk_frames * c->n, 256),
+               i_b = round_up((size_t)chunk_frames * 4, 256), o_b = round_up((size_t)chunk_frames, 256);
+  cudaStream_t streams[2] = {main, c->side};
+  // the side stream starts after work already queued on the caller's stream
+  if (cudaEventRecord(c->ev[0], main) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev[0], 0) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(in_host);
+  for (int f0 = 0, i = 0; f0 < frames; f0 += chunk_frames, ++i) {
+    const int nf = frames - f0 < chunk_frames ? frames - f0 : chunk_frames;
+    unsigned char* base = reinterpret_cast<unsigned char*>(workspace_dev) + (size_t)(i & 1) * per;
+    void* g = base;
+    uint8_t* sy = base + g_b;
+    int32_t* it = reinterpret_cast<int32_t*>(base + g_b + s_b);
+    uint8_t* okb = base + g_b + s_b + i_b;
+    void* ws = base + g_b + s_b + i_b + o_b;
+    cudaStream_t s = streams[i & 1];
+    cudaError_t e = cudaMemcpyAsync(g, src + (size_t)f0 * fbytes, (size_t)nf * fbytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+    st = dec(g, nf, sy, it, okb, ws, s);
+    if (st != NBLDPC_OK) return st;
+    e = cudaMemcpyAsync(out_sym_host + (size_t)f0 * c->n, sy, (size_t)nf * c->n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_iters_host + f0, it, (size_t)nf * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_ok_host + f0, okb, (size_t)nf, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  }
+  // the caller's stream completes only after the side stream's chunks
+  if (cudaEventRecord(c->ev[1], c->side) != cudaSuccess || cudaStreamWaitEvent(main, c->ev[1], 0) != cudaSuccess)
+    return NBLDPC_ERR_CUDA;
   return NBLDPC_OK;
 }
 
@@ -834,10 +902,7 @@ int nbldpc_code_autotune(nbldpc_code* c, const uint8_t* gamma_dev, int frames, i
 
 int nbldpc_decode_host_workspace_size(const nbldpc_code* c, int chunk_frames, size_t* bytes) {
   if (!c || !bytes || chunk_frames <= 0) return NBLDPC_ERR_ARG;
-  const size_t per = round_up((size_t)chunk_frames * c->n * c->q, 256) + round_up((size_t)chunk_frames * c->n, 256) +
-                     round_up((size_t)chunk_frames * 4, 256) + round_up((size_t)chunk_frames, 256) +
-                     round_up(decode_ws_bytes(c, chunk_frames), 256);
-  *bytes = 2 * per;
+  *bytes = 2 * host_chunk_bytes(c, chunk_frames, (size_t)c->n * c->q, decode_ws_bytes(c, chunk_frames));
   return NBLDPC_OK;
 }
 
@@ -847,53 +912,38 @@ int nbldpc_decode_host(const nbldpc_code* cc, const uint8_t* gamma_host, int fra
   nbldpc_code* c = const_cast<nbldpc_code*>(cc);
   if (!c || frames < 0 || max_iters < 0 || chunk_frames <= 0) return NBLDPC_ERR_ARG;
   if (frames == 0) return NBLDPC_OK;
-  if (!gamma_host || !out_sym_host || !out_iters_host || !out_ok_host || !workspace_dev) return NBLDPC_ERR_ARG;
-  if (!aligned(workspace_dev, 256)) return NBLDPC_ERR_ARG;
-  size_t need = 0;
-  nbldpc_decode_host_workspace_size(c, chunk_frames, &need);
-  if (workspace_bytes < need) return NBLDPC_ERR_ARG;
-  int st = cuda_status(cudaGetLastError());
-  if (st != NBLDPC_OK) return st;
-  cudaStream_t main = reinterpret_cast<cudaStream_t>(cuda_stream);
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    if (!c->side) {
-      if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) return NBLDPC_ERR_CUDA;
-      for (auto& ev : c->ev)
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return NBLDPC_ERR_CUDA;
-    }
-  }
-  std::lock_guard<std::mutex> lk(c->mu);  // one host decode at a time per handle (shared side stream)
-  const size_t g_b = round_up((size_t)chunk_frames * c->n * c->q, 256), s_b = round_up((size_t)chunk_frames * c->n, 256),
-               i_b = round_up((size_t)chunk_frames * 4, 256), o_b = round_up((size_t)chunk_frames, 256);
-  const size_t per = need / 2;
-  cudaStream_t streams[2] = {main, c->side};
-  // the side stream starts after work already queued on the caller's stream
-  if (cudaEventRecord(c->ev[0], main) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev[0], 0) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
-  const size_t fbytes = (size_t)c->n * c->q;
-  for (int f0 = 0, i = 0; f0 < frames; f0 += chunk_frames, ++i) {
-    const int nf = frames - f0 < chunk_frames ? frames - f0 : chunk_frames;
-    unsigned char* base = reinterpret_cast<unsigned char*>(workspace_dev) + (size_t)(i & 1) * per;
-    uint8_t* g = base;
-    uint8_t* sy = base + g_b;
-    int32_t* it = reinterpret_cast<int32_t*>(base + g_b + s_b);
-    uint8_t* okb = base + g_b + s_b + i_b;
-    void* ws = base + g_b + s_b + i_b + o_b;
-    cudaStream_t s = streams[i & 1];
-    cudaError_t e = cudaMemcpyAsync(g, gamma_host + (size_t)f0 * fbytes, (size_t)nf * fbytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-    st = launch(c, g, nf, max_iters, early_stop, sy, it, okb, ws, s);
-    if (st != NBLDPC_OK) return st;
-    e = cudaMemcpyAsync(out_sym_host + (size_t)f0 * c->n, sy, (size_t)nf * c->n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_iters_host + f0, it, (size_t)nf * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_ok_host + f0, okb, (size_t)nf, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  }
-  // the caller's stream completes only after the side stream's chunks
-  if (cudaEventRecord(c->ev[1], c->side) != cudaSuccess || cudaStreamWaitEvent(main, c->ev[1], 0) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
+  const size_t per = host_chunk_bytes(c, chunk_frames, (size_t)c->n * c->q, decode_ws_bytes(c, chunk_frames));
+  return host_chunks(c, gamma_host, (size_t)c->n * c->q, frames, out_sym_host, out_iters_host, out_ok_host,
+                     chunk_frames, workspace_dev, workspace_bytes, per, cuda_stream,
+                     [&](const void* in, int nf, uint8_t* sy, int32_t* it, uint8_t* okb, void* ws, cudaStream_t s) {
+                       return launch(c, reinterpret_cast<const uint8_t*>(in), nf, max_iters, early_stop, sy, it, okb,
+                                     ws, s);
+                     });
+}
+
+int nbldpc_fftspa_decode_host_workspace_size(const nbldpc_code* c, int chunk_frames, size_t* bytes) {
+  if (!c || !bytes || chunk_frames <= 0) return NBLDPC_ERR_ARG;
+  if (c->fft_status != NBLDPC_OK) return c->fft_status;
+  *bytes = 2 * host_chunk_bytes(c, chunk_frames, (size_t)c->n * c->q * sizeof(float),
+                                ws_bytes(c->fft_plan, chunk_frames));
   return NBLDPC_OK;
+}
+
+int nbldpc_fftspa_decode_host(const nbldpc_code* cc, const float* prob_host, int frames, int max_iters,
+                              int early_stop, uint8_t* out_sym_host, int32_t* out_iters_host, uint8_t* out_ok_host,
+                              int chunk_frames, void* workspace_dev, size_t workspace_bytes, void* cuda_stream) {
+  nbldpc_code* c = const_cast<nbldpc_code*>(cc);
+  if (!c || frames < 0 || max_iters < 0 || chunk_frames <= 0) return NBLDPC_ERR_ARG;
+  if (c->fft_status != NBLDPC_OK) return c->fft_status;
+  if (frames == 0) return NBLDPC_OK;
+  const size_t fbytes = (size_t)c->n * c->q * sizeof(float);
+  const size_t per = host_chunk_bytes(c, chunk_frames, fbytes, ws_bytes(c->fft_plan, chunk_frames));
+  return host_chunks(c, prob_host, fbytes, frames, out_sym_host, out_iters_host, out_ok_host, chunk_frames,
+                     workspace_dev, workspace_bytes, per, cuda_stream,
+                     [&](const void* in, int nf, uint8_t* sy, int32_t* it, uint8_t* okb, void* ws, cudaStream_t s) {
+                       return fft_launch(c, reinterpret_cast<const float*>(in), nf, max_iters, early_stop, sy, it, okb,
+                                         nullptr, ws, s);
+                     });
 }
 
 }  // extern "C"

@@ -237,3 +237,24 @@ def test_full_size_sampled():
     fer = float((sym.to(torch.int64) != cw).any(1).float().mean())
     assert fer < 0.2
     assert bool((its[ok == 0] == w["max_iters"]).all())      # early stop: unfinished frames ran I_max
+
+
+@pytest.mark.parametrize("chunk", [7, 100, 4096])
+def test_host_buffers_in_chunks_equal_the_device_decode(chunk):
+    """nbldpc_fftspa_decode_host (pinned host rows, two streams, chunked) returns
+    exactly what the device-buffer decode returns for the same frames."""
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    b = I.make_batch(code, 2.0, 57, 333, prob=True)
+    dec = binding.Decoder.from_code(code)
+    want = [t.cpu() for t in dec.fftspa_decode(b.prob.cuda(), 15, 1)]
+    ph = b.prob.contiguous().pin_memory()
+    sym = torch.empty((333, code.n), dtype=torch.uint8).pin_memory()
+    its = torch.empty(333, dtype=torch.int32).pin_memory()
+    ok = torch.empty(333, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(binding.nbldpc_fftspa_decode_host_workspace_size(dec.handle, chunk), dtype=torch.uint8,
+                     device="cuda")
+    stream = torch.cuda.Stream()
+    binding.nbldpc_fftspa_decode_host(dec.handle, ph, 333, 15, 1, sym, its, ok, chunk, ws, stream=stream)
+    stream.synchronize()
+    for a, c in zip((sym, its, ok), want):
+        assert torch.equal(a, c)
