@@ -63,8 +63,12 @@ enum {
  *
  * Checks: every row has degree >= 2, every column degree >= 1.  Build limits
  * (NBLDPC_ERR_UNSUPPORTED beyond them): n_cols < 65535, nnz < 65535, row
- * degree <= 64, column degree <= 64.  The edge order within a row does not
- * change any output (the min-max convolution is commutative and associative).
+ * degree <= 64, column degree <= 64, and the code description (3q + 2(M+1) +
+ * 8 nnz + 2(N+1) bytes in 16-byte sections), the N decisions and one check
+ * group's scratch per group must fit one block's shared memory (227 KB on
+ * GB300: about N = 12000 for a (2,4) binary code).  The edge order within a
+ * row does not change any output (the min-max convolution is commutative and
+ * associative).
  *
  * The handle owns device copies of H, its variable-node view and the GF
  * exponent/logarithm tables, allocated on the device that is current at this

@@ -162,8 +162,11 @@ def _bad_edges(edge_vn: np.ndarray, m: int, dc: int) -> list[int]:
 
 
 def make_regular_code(q: int, n: int, dv: int, dc: int, seed: int, poly: int | None = None,
-                      name: str = "", max_rounds: int = 20000) -> Code:
-    """Seeded regular (dv, dc) code over GF(q) with girth > 4 (see module doc)."""
+                      name: str = "", max_rounds: int = 20000, encoder: bool = True) -> Code:
+    """Seeded regular (dv, dc) code over GF(q) with girth > 4 (see module doc).
+
+    encoder=False skips the row reduction (no codewords can be drawn; rank stays -1):
+    for large codes decoded from random reliabilities."""
     poly = PRIMITIVE_POLY[q] if poly is None else poly
     e_total = n * dv
     if e_total % dc:
@@ -185,7 +188,8 @@ def make_regular_code(q: int, n: int, dv: int, dc: int, seed: int, poly: int | N
     code = Code(q=q, poly=poly, n=n, m=m,
                 row_ptr=(np.arange(m + 1, dtype=np.int32) * dc),
                 col_idx=rows.reshape(-1).astype(np.int32), coef=coef, name=name)
-    _finish(code)
+    if encoder:
+        _finish(code)
     return code
 
 
