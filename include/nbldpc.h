@@ -235,6 +235,23 @@ int nbldpc_code_set_message_bits(nbldpc_code *code, int bits);   /* bits: 8 or 1
 int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
 
 /*
+ * ---- Check-node schedule ------------------------------------------------------
+ *
+ * The forward/backward check-node pass needs 3(d_c - 2) min-max convolutions
+ * per check (F_1..F_{d_c-2}, B_{d_c-2}..B_1 and the d_c - 2 middle beta
+ * values).  Table 1 of the paper counts F and B over d_c - 1 edges each,
+ * 3 d_c - 4 convolutions: the two extra ones (F_{d_c-1} and B_0) feed no
+ * message.  NBLDPC_CNP_TABLE1 computes them anyway, for timing the paper's
+ * operation count; outputs are identical under both schedules.  Applies to
+ * every later single-code decode of the code (a separate kernel); with 16-bit
+ * messages, and in mixed-code batches, it returns NBLDPC_ERR_UNSUPPORTED.
+ */
+#define NBLDPC_CNP_MINIMAL 0
+#define NBLDPC_CNP_TABLE1 1
+int nbldpc_code_set_cnp_schedule(nbldpc_code *code, int schedule);
+int nbldpc_code_get_cnp_schedule(const nbldpc_code *code, int *schedule);
+
+/*
  * ---- FFT-based sum-product decoding (FFT-SPA, Alg. 1) -----------------------
  *
  * The paper's second decoder, in float arithmetic: messages are q symbol

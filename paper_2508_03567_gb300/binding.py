@@ -31,12 +31,15 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_host", "nbldpc_decode_batch_workspace_size", "nbldpc_decode_batch",
             "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
             "nbldpc_code_autotune", "nbldpc_code_set_message_bits", "nbldpc_code_get_message_bits",
+            "nbldpc_code_set_cnp_schedule", "nbldpc_code_get_cnp_schedule",
             "nbldpc_fftspa_workspace_size", "nbldpc_fftspa_decode",
             "nbldpc_fftspa_decode_host_workspace_size", "nbldpc_fftspa_decode_host",
             "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
 NBLDPC_MAX_BATCH_JOBS = 32
+NBLDPC_CNP_MINIMAL = 0
+NBLDPC_CNP_TABLE1 = 1
 
 
 class nbldpc_job(ctypes.Structure):
@@ -91,6 +94,8 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_code_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.nbldpc_code_set_message_bits.argtypes = [vp, ctypes.c_int]
             L.nbldpc_code_get_message_bits.argtypes = [vp, ip]
+            L.nbldpc_code_set_cnp_schedule.argtypes = [vp, ctypes.c_int]
+            L.nbldpc_code_get_cnp_schedule.argtypes = [vp, ip]
             L.nbldpc_fftspa_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_fftspa_decode.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                                vp, sz, vp]
@@ -290,6 +295,16 @@ def nbldpc_code_set_tuning(handle: int, variant: int, frames_per_block: int) -> 
 
 def nbldpc_code_set_message_bits(handle: int, bits: int) -> None:
     _check(lib().nbldpc_code_set_message_bits(handle, int(bits)), "nbldpc_code_set_message_bits")
+
+
+def nbldpc_code_set_cnp_schedule(handle: int, schedule: int) -> None:
+    _check(lib().nbldpc_code_set_cnp_schedule(handle, int(schedule)), "nbldpc_code_set_cnp_schedule")
+
+
+def nbldpc_code_get_cnp_schedule(handle: int) -> int:
+    v = ctypes.c_int()
+    _check(lib().nbldpc_code_get_cnp_schedule(handle, ctypes.byref(v)), "nbldpc_code_get_cnp_schedule")
+    return v.value
 
 
 def nbldpc_code_get_message_bits(handle: int) -> int:

@@ -13,13 +13,19 @@
 
 namespace nbldpc {
 
-// Address of the decode kernel for layout variant v and mb-byte messages of
-// this unit's field order.
-const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb) {
+// Address of the decode kernel for layout variant v, mb-byte messages and the
+// check-node schedule t1 (1: Table 1's 3 d_c - 4 convolutions, 8-bit messages
+// only) of this unit's field order; null when there is none.
+const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1) {
 #if NBLDPC_KQ == 0
   (void)v;
-  return mb == 1 ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
+  return (mb == 1 && !t1) ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
 #else
+  if (t1) {
+    if (mb != 1) return nullptr;
+    return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, true>)
+             : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1, true>);
+  }
   if (mb == 2)
     return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 2>)
              : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 2>);

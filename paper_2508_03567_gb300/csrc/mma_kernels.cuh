@@ -347,7 +347,7 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
 // slot's message area ([nnz][q] bytes).
-template <class g, int MB>
+template <class g, int MB, bool T1>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
@@ -596,6 +596,10 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
           fprev = job.dmax + j;
         }
         depermute(vec16(fprev), e0 + d - 1);               // beta_{d-1} from F_{d-2}
+        if constexpr (T1) {          // Table 1 schedule: F_{d-1} into the scratch vector, unused
+          mm_conv<g, MB == 1>(vec(fprev), vec(d - 1), vec16(2 * job.dmax + 2), cl, gmask);
+          group_sync<g::G>(gmask);
+        }
         // backward: B_{d-1} = P_{d-1}; beta_j from F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j
         int bcur = d - 1;
         int pp = 0;
@@ -612,6 +616,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
           pp ^= 1;
         }
         depermute(vec16(bcur), e0);                        // beta_0 from B_1
+        if constexpr (T1)            // Table 1 schedule: B_0 into the scratch vector, unused
+          mm_conv<g, MB == 1>(vec(bcur), vec(0), vec16(2 * job.dmax + 2), cl, gmask);
         group_sync<g::G>(gmask);
       }
     };
@@ -658,20 +664,21 @@ template <int QSEL, int VSEL> struct MinBlocks {
 };
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
-template <int Q, int VSEL, int MB>
+template <int Q, int VSEL, int MB, bool T1 = false>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                                uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   if constexpr (VSEL >= 0) {
-    decode_frame<Geo<Q, VSEL>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, VSEL>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (job.variant == 0) {
-    decode_frame<Geo<Q, 0>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 0>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else {
-    decode_frame<Geo<Q, 1>, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 1>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   }
 }
 
 // MB: message bytes per symbol (1: 8-bit messages; 2: 16-bit, single-field kernels only).
-template <int QSEL, int VSEL, int MB>
+// T1: the Table 1 check-node schedule (3 d_c - 4 convolutions; single-field kernels only).
+template <int QSEL, int VSEL, int MB, bool T1 = false>
 __global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
@@ -703,7 +710,7 @@ __global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kern
       slot_sync(bar_id, nthr);
     }
     if constexpr (QSEL != 0) {
-      decode_variant<QSEL, VSEL, MB>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      decode_variant<QSEL, VSEL, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
     } else {
       switch (job.q) {
         case 2: decode_variant<2, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;

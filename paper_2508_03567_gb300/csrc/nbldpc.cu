@@ -44,6 +44,7 @@ struct nbldpc_code {
   nbldpc::CodeBlob off{};
   int variant = 0;                     // layout variant used by every decode of this code
   int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
+  int cnp_schedule = NBLDPC_CNP_MINIMAL;   // check-node convolutions: 3(d-2) or Table 1's 3d-4
   Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
   int fft_status = NBLDPC_ERR_UNSUPPORTED;   // FFT-SPA launch shape below valid when NBLDPC_OK
   int fft_dc = 0, fft_dv = 0;          // degree buckets of the FFT-SPA kernel (dc 0: q <= 64 lane-per-edge path)
@@ -90,15 +91,15 @@ bool build_field(int q, uint32_t poly, std::vector<uint8_t>& exp2, std::vector<u
 }  // namespace
 
 namespace nbldpc {   // defined in kernels.cu, one translation unit per field order
-const void* kernel_q0(int v, int mb);
-const void* kernel_q2(int v, int mb);
-const void* kernel_q4(int v, int mb);
-const void* kernel_q8(int v, int mb);
-const void* kernel_q16(int v, int mb);
-const void* kernel_q32(int v, int mb);
-const void* kernel_q64(int v, int mb);
-const void* kernel_q128(int v, int mb);
-const void* kernel_q256(int v, int mb);
+const void* kernel_q0(int v, int mb, int t1);
+const void* kernel_q2(int v, int mb, int t1);
+const void* kernel_q4(int v, int mb, int t1);
+const void* kernel_q8(int v, int mb, int t1);
+const void* kernel_q16(int v, int mb, int t1);
+const void* kernel_q32(int v, int mb, int t1);
+const void* kernel_q64(int v, int mb, int t1);
+const void* kernel_q128(int v, int mb, int t1);
+const void* kernel_q256(int v, int mb, int t1);
 const void* fft_kernel_q2(int dc, int dv, int* threads);
 const void* fft_kernel_q4(int dc, int dv, int* threads);
 const void* fft_kernel_q8(int dc, int dv, int* threads);
@@ -111,19 +112,24 @@ const void* fft_kernel_q256(int dc, int dv, int* threads);
 
 namespace {
 
-// kernel compiled for one field order, layout variant and message width, or
-// for every field order (q = 0, 8-bit messages)
-const void* kernel_for(int q, int v, int mb) {
+// Kernel mode: 1 = 8-bit messages, 2 = 16-bit messages, 3 = 8-bit messages with
+// the Table 1 check-node schedule (each a separate kernel instantiation).
+int kmode(const nbldpc_code* c) { return c->mb == 2 ? 2 : (c->cnp_schedule == NBLDPC_CNP_TABLE1 ? 3 : 1); }
+
+// kernel compiled for one field order, layout variant and kernel mode, or for
+// every field order (q = 0, mode 1)
+const void* kernel_for(int q, int v, int km) {
+  const int mb = km == 2 ? 2 : 1, t1 = km == 3 ? 1 : 0;
   switch (q) {
-    case 0: return nbldpc::kernel_q0(-1, mb);
-    case 2: return nbldpc::kernel_q2(v, mb);
-    case 4: return nbldpc::kernel_q4(v, mb);
-    case 8: return nbldpc::kernel_q8(v, mb);
-    case 16: return nbldpc::kernel_q16(v, mb);
-    case 32: return nbldpc::kernel_q32(v, mb);
-    case 64: return nbldpc::kernel_q64(v, mb);
-    case 128: return nbldpc::kernel_q128(v, mb);
-    case 256: return nbldpc::kernel_q256(v, mb);
+    case 0: return nbldpc::kernel_q0(-1, mb, t1);
+    case 2: return nbldpc::kernel_q2(v, mb, t1);
+    case 4: return nbldpc::kernel_q4(v, mb, t1);
+    case 8: return nbldpc::kernel_q8(v, mb, t1);
+    case 16: return nbldpc::kernel_q16(v, mb, t1);
+    case 32: return nbldpc::kernel_q32(v, mb, t1);
+    case 64: return nbldpc::kernel_q64(v, mb, t1);
+    case 128: return nbldpc::kernel_q128(v, mb, t1);
+    case 256: return nbldpc::kernel_q256(v, mb, t1);
   }
   return nullptr;
 }
@@ -161,18 +167,18 @@ int group_bytes(int q, int dmax, int mb) {
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
 std::mutex g_attr_mu;
-bool g_attr_done[64][33] = {};
+bool g_attr_done[64][49] = {};
 
-int kernel_slot(int q, int v, int mb) {
-  return q == 0 ? 0 : 1 + 4 * (nbldpc::ilog2(q) - 1) + 2 * (mb - 1) + (v ? 1 : 0);
+int kernel_slot(int q, int v, int km) {
+  return q == 0 ? 0 : 1 + 6 * (nbldpc::ilog2(q) - 1) + 2 * (km - 1) + (v ? 1 : 0);
 }
 
-int prepare_kernel(int q, int v, int mb, int dev, int smem_optin) {
+int prepare_kernel(int q, int v, int km, int dev, int smem_optin) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
-  const void* k = kernel_for(q, v, mb);
+  const void* k = kernel_for(q, v, km);
   if (!k) return NBLDPC_ERR_UNSUPPORTED;
-  bool& done = g_attr_done[dev][kernel_slot(q, v, mb)];
+  bool& done = g_attr_done[dev][kernel_slot(q, v, km)];
   if (!done) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
       return NBLDPC_ERR_CUDA;
@@ -190,8 +196,8 @@ CodeNeeds needs_of(const nbldpc_code* c, int variant, int mb) {
   return CodeNeeds{c->q, variant, mb, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q * mb, 256)};
 }
 
-// Plan a launch of kernel (kq, kv, kmb) with fpb frame slots per block for a set of codes.
-int make_plan(int kq, int kv, int kmb, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
+// Plan a launch of kernel (kq, kv, kernel mode km) with fpb frame slots per block for a set of codes.
+int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -218,9 +224,9 @@ int make_plan(int kq, int kv, int kmb, int fpb, const CodeNeeds* cs, int nc, Pla
   pl.slot_smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16 + scratch), 16);
   pl.smem = fpb * pl.slot_smem;
   if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
-  int st = prepare_kernel(kq, kv, kmb, dev, optin);
+  int st = prepare_kernel(kq, kv, km, dev, optin);
   if (st != NBLDPC_OK) return st;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv, kmb), pl.threads, pl.smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv, km), pl.threads, pl.smem) !=
       cudaSuccess)
     return NBLDPC_ERR_CUDA;
   if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
@@ -246,7 +252,7 @@ int default_fpb(const nbldpc_code* c) {
 int configure(nbldpc_code* c, int variant, int fpb) {
   Plan pl{};
   const CodeNeeds need = needs_of(c, variant, c->mb);
-  const int st = make_plan(c->q, variant, c->mb, fpb, &need, 1, &pl);
+  const int st = make_plan(c->q, variant, kmode(c), fpb, &need, 1, &pl);
   if (st != NBLDPC_OK) return st;
   c->variant = variant;
   c->plan = pl;
@@ -312,7 +318,7 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
   lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant, c->mb), c->plan, lp, grid_for(c->plan, frames), ws,
+  return launch_plan(kernel_for(c->q, c->variant, kmode(c)), c->plan, lp, grid_for(c->plan, frames), ws,
                      reinterpret_cast<uint8_t*>(ws) + 256, st);
 }
 
@@ -537,7 +543,7 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
   lp.jobs[0] = job_desc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, 0);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant, c->mb), pl, lp, grid, scratch,
+  return launch_plan(kernel_for(c->q, c->variant, kmode(c)), pl, lp, grid, scratch,
                      reinterpret_cast<uint8_t*>(scratch) + 256,
                      reinterpret_cast<cudaStream_t>(cuda_stream));
 }
@@ -721,6 +727,7 @@ int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
 
 int nbldpc_code_set_message_bits(nbldpc_code* c, int bits) {
   if (!c || (bits != 8 && bits != 16)) return NBLDPC_ERR_ARG;
+  if (bits == 16 && c->cnp_schedule == NBLDPC_CNP_TABLE1) return NBLDPC_ERR_UNSUPPORTED;
   const int old = c->mb;
   c->mb = bits / 8;
   const int st = configure(c, c->variant, c->plan.fpb);
@@ -731,6 +738,22 @@ int nbldpc_code_set_message_bits(nbldpc_code* c, int bits) {
 int nbldpc_code_get_message_bits(const nbldpc_code* c, int* bits) {
   if (!c || !bits) return NBLDPC_ERR_ARG;
   *bits = 8 * c->mb;
+  return NBLDPC_OK;
+}
+
+int nbldpc_code_set_cnp_schedule(nbldpc_code* c, int schedule) {
+  if (!c || (schedule != NBLDPC_CNP_MINIMAL && schedule != NBLDPC_CNP_TABLE1)) return NBLDPC_ERR_ARG;
+  if (schedule == NBLDPC_CNP_TABLE1 && c->mb != 1) return NBLDPC_ERR_UNSUPPORTED;
+  const int old = c->cnp_schedule;
+  c->cnp_schedule = schedule;
+  const int st = configure(c, c->variant, c->plan.fpb);   // the schedule is a separate kernel
+  if (st != NBLDPC_OK) c->cnp_schedule = old;
+  return st;
+}
+
+int nbldpc_code_get_cnp_schedule(const nbldpc_code* c, int* schedule) {
+  if (!c || !schedule) return NBLDPC_ERR_ARG;
+  *schedule = c->cnp_schedule;
   return NBLDPC_OK;
 }
 
@@ -787,7 +810,7 @@ static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) 
   for (int i = 0; i < n_jobs; ++i) {
     const nbldpc_code* c = jobs[i].code;
     if (!c || jobs[i].frames < 0 || jobs[i].max_iters < 0) return NBLDPC_ERR_ARG;
-    if (c->mb != 1) return NBLDPC_ERR_UNSUPPORTED;   // mixed-code launches carry 8-bit messages
+    if (kmode(c) != 1) return NBLDPC_ERR_UNSUPPORTED;   // mixed-code launches: 8-bit messages, minimal schedule
     need[i] = needs_of(c, c->variant, 1);
     if (c->plan.fpb < fpb) fpb = c->plan.fpb;
     t += jobs[i].frames;
@@ -844,7 +867,7 @@ int nbldpc_code_autotune_workspace_size(const nbldpc_code* c, int frames, size_t
     for (int fpb = 1; fpb <= 8; fpb *= 2) {
       Plan pl{};
       const CodeNeeds need = needs_of(c, v, c->mb);
-      if (make_plan(c->q, v, c->mb, fpb, &need, 1, &pl) != NBLDPC_OK) continue;
+      if (make_plan(c->q, v, kmode(c), fpb, &need, 1, &pl) != NBLDPC_OK) continue;
       const size_t w = ws_bytes(pl, frames);
       if (w > mx) mx = w;
     }

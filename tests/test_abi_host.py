@@ -95,3 +95,10 @@ def test_fftspa_arguments_are_checked_without_a_device(lib):
     b = ctypes.c_size_t()
     assert L.nbldpc_fftspa_workspace_size(None, 4, ctypes.byref(b)) == lib.NBLDPC_ERR_ARG
     assert L.nbldpc_fftspa_decode(None, None, 4, 5, 1, None, None, None, None, None, 0, None) == lib.NBLDPC_ERR_ARG
+
+
+def test_cnp_schedule_arguments_are_checked(lib):
+    L = lib.lib()
+    assert L.nbldpc_code_set_cnp_schedule(None, lib.NBLDPC_CNP_MINIMAL) == lib.NBLDPC_ERR_ARG
+    s = ctypes.c_int()
+    assert L.nbldpc_code_get_cnp_schedule(None, ctypes.byref(s)) == lib.NBLDPC_ERR_ARG

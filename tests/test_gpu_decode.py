@@ -393,3 +393,43 @@ def test_mixed_batch_rejects_sixteen_bit_codes():
     with pytest.raises(binding.NbldpcError) as ei:
         binding.nbldpc_decode_batch_workspace_size([(dec.handle, g, 2, 5, 1, *out)])
     assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
+
+
+# --------------------------------------------------------------- Table 1 check-node schedule
+@pytest.mark.parametrize("name", ["gf64_n576_dv2_dc4", "gf32_n600_dv3_dc6", "gf256_n128_dv2_dc8", "gf4_n48_dv2_dc4"])
+def test_table1_schedule_gives_identical_outputs(name):
+    """3 d_c - 4 convolutions per check (F_{d-1}, B_0 computed and unused): same results as the oracle,
+    for both layout variants."""
+    code = I.workload_code(name)
+    g = I.make_batch(code, 1.5, 8080, 16).gamma.numpy()
+    dec = binding.Decoder.from_code(code)
+    binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_TABLE1)
+    assert binding.nbldpc_code_get_cnp_schedule(dec.handle) == binding.NBLDPC_CNP_TABLE1
+    gd = torch.as_tensor(g).cuda()
+    want = oracle.decode(code, g, 20, 1, threads=THREADS)
+    for v in (0, 1):
+        dec.set_tuning(v, 1)
+        assert_same([t.cpu().numpy() for t in dec.decode(gd, 20, 1)], want, f"{name} table1 v{v}")
+    binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_MINIMAL)
+    assert_same([t.cpu().numpy() for t in dec.decode(gd, 20, 1)], want, f"{name} back to minimal")
+
+
+def test_table1_schedule_limits():
+    """The Table 1 schedule is an 8-bit single-code kernel: 16-bit messages and mixed batches refuse it."""
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    dec = binding.Decoder.from_code(code)
+    binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_TABLE1)
+    with pytest.raises(binding.NbldpcError) as ei:
+        dec.set_message_bits(16)
+    assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
+    g = torch.zeros((2, code.n, code.q), dtype=torch.uint8, device="cuda")
+    out = (torch.empty((2, code.n), dtype=torch.uint8, device="cuda"), torch.empty(2, dtype=torch.int32, device="cuda"),
+           torch.empty(2, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(binding.NbldpcError) as ei:
+        binding.nbldpc_decode_batch_workspace_size([(dec.handle, g, 2, 5, 1, *out)])
+    assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
+    binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_MINIMAL)
+    dec.set_message_bits(16)
+    with pytest.raises(binding.NbldpcError) as ei:
+        binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_TABLE1)
+    assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
