@@ -366,6 +366,88 @@ int nbldpc_decode_noalloc(const nbldpc_code *code, const uint8_t *gamma_dev, int
                           uint8_t *out_ok_dev, void *cuda_stream);
 
 /*
+ * ---- Serving: continuous batching of decode requests -------------------------
+ *
+ * A server queues requests (frames of one code in host memory), admits them in
+ * arrival order while the device bytes they keep resident (reliabilities,
+ * outputs, and the workspace of the launches in flight) fit a budget, and
+ * launches the admitted requests as one mixed-code persistent decode
+ * (nbldpc_decode_batch, up to max_jobs requests) as soon as one of its streams
+ * is free; requests arriving meanwhile go into the next launch, concurrently
+ * with the launches still in flight.  "Plain" mode is the reference point: one
+ * stream, one fixed-iteration nbldpc_decode per request (early stop off).  A
+ * request larger than the whole budget is admitted alone once nothing else is
+ * resident.  Each frame decodes to the same outputs alone or in any mix.
+ *
+ * The scheduler runs inside nbldpc_server_poll (no thread, no device-side
+ * wait); one host thread drives a server.  The device work goes through an
+ * executor: the library's CUDA executor (nbldpc_server_create) or callbacks
+ * (nbldpc_server_create_custom, e.g. a host fake that tests the scheduler
+ * without a GPU).  The paper has no serving layer; this is the batching and
+ * latency layer over Alg. 2 decodes.
+ */
+typedef struct nbldpc_request {
+  const nbldpc_code *code;
+  const uint8_t *gamma_host;      /* [frames][n_cols][q] uint8; pinned for asynchronous copies */
+  int frames;                     /* >= 1 */
+  int max_iters;                  /* I_max >= 0 */
+  int early_stop;                 /* continuous mode only; plain mode decodes fixed iterations */
+  uint8_t *out_sym_host;          /* [frames][n_cols], written by the time the request completes */
+  int32_t *out_iters_host;        /* [frames] */
+  uint8_t *out_ok_host;           /* [frames] */
+  void *user;                     /* caller's tag, passed back to custom executors */
+  uint64_t id;                    /* set by nbldpc_server_submit */
+} nbldpc_request;
+
+typedef struct nbldpc_server_executor {
+  void *ctx;
+  /* resident device bytes of one request while admitted or in flight */
+  size_t (*request_bytes)(void *ctx, const nbldpc_request *req);
+  /* workspace bytes of one launch of these requests */
+  size_t (*launch_bytes)(void *ctx, const nbldpc_request *const *reqs, int n, int plain);
+  /* queue copies in, the decode and copies out on stream index `stream`; a token for done/finish */
+  int (*start)(void *ctx, const nbldpc_request *const *reqs, int n, int stream, int plain, uint64_t *token);
+  /* 1: the launch and its copies completed, 0: not yet, < 0: error status (non-blocking) */
+  int (*done)(void *ctx, uint64_t token);
+  /* release what the launch holds (called once, after done returned 1) */
+  int (*finish)(void *ctx, uint64_t token);
+} nbldpc_server_executor;
+
+typedef struct nbldpc_server_stats {
+  size_t used_bytes;              /* admitted requests + launches in flight (their requests and workspace) */
+  size_t peak_bytes;
+  uint64_t launches, submitted, completed;
+  int waiting, admitted, in_flight;
+} nbldpc_server_stats;
+
+typedef struct nbldpc_server nbldpc_server;
+
+/* Server with the library's CUDA executor on the current device: `streams`
+ * (>= 1) streams owned by the server, device buffers from the stream-ordered
+ * allocator, budget_bytes of resident device memory, up to max_jobs
+ * (1..NBLDPC_MAX_BATCH_JOBS) requests per launch; plain != 0: plain mode. */
+int nbldpc_server_create(size_t budget_bytes, int streams, int max_jobs, int plain, nbldpc_server **out);
+
+/* Server whose device work goes to `executor` (copied; its ctx must outlive the server). */
+int nbldpc_server_create_custom(const nbldpc_server_executor *executor, size_t budget_bytes, int streams,
+                                int max_jobs, int plain, nbldpc_server **out);
+
+/* Queue a request (copied; its host buffers must stay valid until it completes); *id receives its id.
+ * The CUDA executor needs code, gamma_host and the three output buffers (NBLDPC_ERR_ARG otherwise); a
+ * custom executor's server checks only frames >= 1 and max_iters >= 0. */
+int nbldpc_server_submit(nbldpc_server *server, const nbldpc_request *req, uint64_t *id);
+
+/* One scheduling round: retire completed launches, admit, launch on free
+ * streams; then write up to `capacity` ids of completed requests (in
+ * completion order; the rest come with later calls) and their count. */
+int nbldpc_server_poll(nbldpc_server *server, uint64_t *done_ids, int capacity, int *n_done);
+
+int nbldpc_server_stats_get(const nbldpc_server *server, nbldpc_server_stats *stats);
+
+/* Wait for launches in flight (their outputs are written), then free the server; NULL is accepted. */
+void nbldpc_server_destroy(nbldpc_server *server);
+
+/*
  * Number of decode-kernel launches the calls above queued since the library
  * was loaded (all threads, all handles).  Launch accounting for benchmarks.
  */

@@ -34,6 +34,8 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_code_set_cnp_schedule", "nbldpc_code_get_cnp_schedule",
             "nbldpc_fftspa_workspace_size", "nbldpc_fftspa_decode",
             "nbldpc_fftspa_decode_host_workspace_size", "nbldpc_fftspa_decode_host",
+            "nbldpc_server_create", "nbldpc_server_create_custom", "nbldpc_server_submit", "nbldpc_server_poll",
+            "nbldpc_server_stats_get", "nbldpc_server_destroy",
             "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
             "nbldpc_status_string")
 
@@ -53,6 +55,32 @@ class nbldpc_tune_result(ctypes.Structure):
 
 _lib = None
 _lock = threading.Lock()
+
+
+class nbldpc_request(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("gamma_host", ctypes.c_void_p), ("frames", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("early_stop", ctypes.c_int), ("out_sym_host", ctypes.c_void_p),
+                ("out_iters_host", ctypes.c_void_p), ("out_ok_host", ctypes.c_void_p), ("user", ctypes.c_void_p),
+                ("id", ctypes.c_uint64)]
+
+
+_REQP = ctypes.POINTER(nbldpc_request)
+REQUEST_BYTES_FN = ctypes.CFUNCTYPE(ctypes.c_size_t, ctypes.c_void_p, _REQP)
+LAUNCH_BYTES_FN = ctypes.CFUNCTYPE(ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(_REQP), ctypes.c_int, ctypes.c_int)
+START_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_REQP), ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, ctypes.POINTER(ctypes.c_uint64))
+TOKEN_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
+
+
+class nbldpc_server_executor(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("request_bytes", REQUEST_BYTES_FN), ("launch_bytes", LAUNCH_BYTES_FN),
+                ("start", START_FN), ("done", TOKEN_FN), ("finish", TOKEN_FN)]
+
+
+class nbldpc_server_stats(ctypes.Structure):
+    _fields_ = [("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64),
+                ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("waiting", ctypes.c_int),
+                ("admitted", ctypes.c_int), ("in_flight", ctypes.c_int)]
 
 
 class NbldpcError(RuntimeError):
@@ -102,6 +130,15 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_fftspa_decode_host_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_fftspa_decode_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                                     ctypes.c_int, vp, sz, vp]
+            srvp = ctypes.POINTER(ctypes.c_void_p)
+            L.nbldpc_server_create.argtypes = [sz, ctypes.c_int, ctypes.c_int, ctypes.c_int, srvp]
+            L.nbldpc_server_create_custom.argtypes = [ctypes.POINTER(nbldpc_server_executor), sz, ctypes.c_int,
+                                                      ctypes.c_int, ctypes.c_int, srvp]
+            L.nbldpc_server_submit.argtypes = [vp, ctypes.POINTER(nbldpc_request), ctypes.POINTER(ctypes.c_uint64)]
+            L.nbldpc_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ip]
+            L.nbldpc_server_stats_get.argtypes = [vp, ctypes.POINTER(nbldpc_server_stats)]
+            L.nbldpc_server_destroy.argtypes = [vp]
+            L.nbldpc_server_destroy.restype = None
             L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]

@@ -2,7 +2,7 @@
 
 The kernel translation units (min-max: one per field order plus the one serving
 every field order; FFT-SPA: one per field order) compile in parallel; the host
-unit holds the C ABI.
+units hold the C ABI (decoders; serving scheduler and its CUDA executor).
 """
 from __future__ import annotations
 
@@ -40,6 +40,7 @@ def _units():
     units = [(os.path.join(CSRC, "kernels.cu"), f"kernels_q{q}.o", [f"-DNBLDPC_KQ={q}"]) for q in KERNEL_UNITS]
     units += [(os.path.join(CSRC, "fftspa.cu"), f"fftspa_q{q}.o", [f"-DNBLDPC_FQ={q}"]) for q in FFT_UNITS]
     units.append((os.path.join(CSRC, "nbldpc.cu"), "nbldpc.o", []))
+    units.append((os.path.join(CSRC, "server.cu"), "server.o", []))
     return units
 
 

@@ -2,49 +2,48 @@
 
 A request is a group of frames of one code (reliabilities in host memory)
 that arrives at some time and completes when its decided symbols, iteration
-counts and ok flags are back in host memory.  The server
-
-* queues arriving requests and admits them in arrival order while the bytes
-  they keep resident on the device (reliabilities, outputs, and the message
-  workspace of the launches in flight) stay within a budget;
-* launches the admitted requests as one mixed-code persistent decode
-  (nbldpc_decode_batch, up to 32 requests per launch) as soon as one of its
-  streams is free, so requests that arrive while others are on the GPU run
-  in the next launch, concurrently with the launches still in flight;
-* retires launches as their completion events fire and releases their bytes.
+counts and ok flags are back in host memory.  The scheduler is native
+(nbldpc_server_* in the C ABI): it queues arriving requests, admits them in
+arrival order while the device bytes they keep resident (reliabilities,
+outputs, and the workspace of the launches in flight) fit a budget, launches
+the admitted requests as one mixed-code persistent decode (up to 32 per
+launch) as soon as one of its streams is free, and retires launches as their
+completion events fire.  Requests arriving while others are on the GPU run in
+the next launch, concurrently with the launches still in flight.
 
 At low load every request runs alone (short latency); as load grows the
 streams stay busy and launches carry more requests (throughput).  Each
 frame's result depends only on its own reliabilities (Alg. 2 has no
 interaction between frames), so a request decodes to the same outputs alone
-or in any mix.
+or in any mix.  "Plain" mode is the reference point: one fixed-iteration
+launch per request, one stream, in arrival order.
 
-The "plain" mode is the reference point: one fixed-iteration launch per
-request, one stream, in arrival order.
-
-The scheduling logic is separate from the device work (an executor object),
-so it is tested on the CPU with a fake executor.
+This module is the Python face of that scheduler: `Server` with the
+library's CUDA executor (`CudaExecutor` names the decoders and iteration
+settings), or with any Python object that implements the executor calls
+(used on the CPU with a fake executor to test the scheduling logic).
 """
 from __future__ import annotations
 
-import collections
+import ctypes
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import torch
+
+from . import binding
 
 
 @dataclass
 class Request:
     rid: int
-    code: int                      # index into the server's decoder list
+    code: int                      # index into the executor's decoder list
     gamma: torch.Tensor            # host, [frames, n, q] uint8 (pinned for asynchronous copies)
     t_arrival: float = 0.0
-    sym: torch.Tensor | None = None      # host [frames, n] uint8, filled on completion
+    sym: torch.Tensor | None = None      # host [frames, n] uint8, written by completion
     iters: torch.Tensor | None = None    # host [frames] int32
     ok: torch.Tensor | None = None       # host [frames] uint8
-    t_admit: float = -1.0
-    t_launch: float = -1.0
+    t_launch: float = -1.0               # set by Python executors' start (the native executor does not report it)
     t_done: float = -1.0
 
     @property
@@ -56,105 +55,174 @@ class Request:
         return self.t_done - self.t_arrival
 
 
-@dataclass
-class _Launch:
-    requests: list
-    token: object
-    reserved: int
-    stream: int
+class CudaExecutor:
+    """The library's CUDA executor for a Server: copies in, nbldpc_decode_batch (plain mode: one
+    fixed-iteration nbldpc_decode per request), copies out, one event per launch, device buffers from
+    the stream-ordered allocator.  Holds the decoders that Request.code indexes and the iteration
+    settings of every request."""
+
+    def __init__(self, decoders, max_iters: int, early_stop: int = 1, device="cuda", streams: int = 3):
+        self.decs = decoders
+        self.max_iters = int(max_iters)
+        self.early_stop = int(early_stop)
+        self.dev = torch.device(device)
+        self.streams = int(streams)
 
 
 class Server:
-    """Admission, grouping and retirement; device work goes to `executor`.
+    """Native scheduler; device work by `executor` (a CudaExecutor, or a Python object with
+    request_bytes(req), launch_bytes(reqs, plain), start(reqs, stream, plain) -> token,
+    done(token) -> bool and finish(token))."""
 
-    executor interface:
-      request_bytes(req) -> int          resident device bytes of one request
-      launch_bytes(reqs, plain) -> int   workspace of one launch of these requests
-      start(reqs, stream_index, plain)   queue copies + decode + copies back, return a token
-      done(token) -> bool                completion test (non-blocking)
-      finish(token)                      release device buffers of a completed launch
-    """
+    POLL_BATCH = 256
 
     def __init__(self, executor, budget_bytes: int = 8 << 30, streams: int = 3, max_jobs: int = 32,
                  mode: str = "continuous", clock=time.perf_counter):
         if mode not in ("continuous", "plain"):
             raise ValueError(mode)
-        self.ex = executor
         self.budget = int(budget_bytes)
-        self.streams = 1 if mode == "plain" else int(streams)
-        self.max_jobs = 1 if mode == "plain" else int(max_jobs)
         self.mode = mode
         self.clock = clock
-        self.waiting = collections.deque()     # arrived, not admitted
-        self.admitted = collections.deque()    # device bytes reserved, not launched
-        self.inflight: list[_Launch] = []
-        self.used = 0
-        self.peak_used = 0
-        self.launches = 0
         self.completed: list[Request] = []
+        self._ex = executor
+        self._native = isinstance(executor, CudaExecutor)
+        self._tags: dict[int, Request] = {}     # user tag -> request (submitted, not completed)
+        self._ids: dict[int, Request] = {}      # server id -> request
+        self._next_tag = 1
+        self._tokens: dict[int, object] = {}   # Python executor tokens by native token
+        self._next_token = 1
+        self._h = ctypes.c_void_p()
+        L = binding.lib()
+        plain = 1 if mode == "plain" else 0
+        if self._native:
+            if executor.dev.index is not None:        # the server works on the current device
+                torch.cuda.set_device(executor.dev.index)
+            st = L.nbldpc_server_create(self.budget, int(streams), int(max_jobs), plain, ctypes.byref(self._h))
+        else:
+            self._callbacks = self._make_callbacks()
+            exs = binding.nbldpc_server_executor(None, *self._callbacks)
+            st = L.nbldpc_server_create_custom(ctypes.byref(exs), self.budget, int(streams), int(max_jobs), plain,
+                                               ctypes.byref(self._h))
+        binding._check(st, "nbldpc_server_create")
+        self._buf = (ctypes.c_uint64 * self.POLL_BATCH)()
+
+    # ---- Python executors behind the native scheduler
+    def _make_callbacks(self):
+        ex = self._ex
+
+        def reqs_of(arr, n):
+            return [self._tags[arr[i].contents.user] for i in range(n)]
+
+        def request_bytes(_ctx, rp):
+            try:
+                return int(ex.request_bytes(self._tags[rp.contents.user]))
+            except Exception:  # noqa: BLE001 - a callback must not raise through C
+                return 0
+
+        def launch_bytes(_ctx, arr, n, plain):
+            try:
+                return int(ex.launch_bytes(reqs_of(arr, n), bool(plain)))
+            except Exception:  # noqa: BLE001
+                return 0
+
+        def start(_ctx, arr, n, stream, plain, tok):
+            try:
+                reqs = reqs_of(arr, n)
+                now = self.clock()
+                for r in reqs:
+                    r.t_launch = now
+                k = self._next_token
+                self._next_token += 1
+                self._tokens[k] = ex.start(reqs, int(stream), bool(plain))
+                tok[0] = k
+                return binding.NBLDPC_OK
+            except Exception:  # noqa: BLE001
+                return binding.NBLDPC_ERR_ARG
+
+        def done(_ctx, k):
+            try:
+                return 1 if ex.done(self._tokens[k]) else 0
+            except Exception:  # noqa: BLE001
+                return binding.NBLDPC_ERR_ARG
+
+        def finish(_ctx, k):
+            try:
+                ex.finish(self._tokens.pop(k))
+                return binding.NBLDPC_OK
+            except Exception:  # noqa: BLE001
+                return binding.NBLDPC_ERR_ARG
+
+        return (binding.REQUEST_BYTES_FN(request_bytes), binding.LAUNCH_BYTES_FN(launch_bytes),
+                binding.START_FN(start), binding.TOKEN_FN(done), binding.TOKEN_FN(finish))
 
     # ---- arrivals
     def submit(self, req: Request, now: float | None = None) -> None:
         req.t_arrival = self.clock() if now is None else now
-        self.waiting.append(req)
+        tag = self._next_tag
+        self._next_tag += 1
+        r = binding.nbldpc_request()
+        r.frames = req.frames
+        r.user = tag
+        if self._native:
+            d = self._ex.decs[req.code]
+            if not req.gamma.is_contiguous():
+                raise ValueError("request reliabilities must be contiguous host memory")
+            req.sym = torch.empty((req.frames, d.n), dtype=torch.uint8, pin_memory=True)
+            req.iters = torch.empty((req.frames,), dtype=torch.int32, pin_memory=True)
+            req.ok = torch.empty((req.frames,), dtype=torch.uint8, pin_memory=True)
+            r.code = d.handle
+            r.gamma_host = req.gamma.data_ptr()
+            r.max_iters = self._ex.max_iters
+            r.early_stop = self._ex.early_stop
+            r.out_sym_host = req.sym.data_ptr()
+            r.out_iters_host = req.iters.data_ptr()
+            r.out_ok_host = req.ok.data_ptr()
+        self._tags[tag] = req
+        rid = ctypes.c_uint64()
+        binding._check(binding.lib().nbldpc_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
+                       "nbldpc_server_submit")
+        self._ids[rid.value] = req
+        req._tag = tag
 
     # ---- one scheduling round
     def poll(self) -> list[Request]:
         done = []
-        now = self.clock()
-        still = []
-        for ln in self.inflight:
-            if self.ex.done(ln.token):
-                self.ex.finish(ln.token)
-                self.used -= ln.reserved
-                for r in ln.requests:
-                    r.t_done = now
-                done.extend(ln.requests)
-            else:
-                still.append(ln)
-        self.inflight = still
-        # admission in arrival order, against the budget (a request larger than
-        # the whole budget is admitted alone once nothing else is resident)
-        while self.waiting:
-            r = self.waiting[0]
-            b = self.ex.request_bytes(r)
-            if self.used + b > self.budget and (self.used > 0 or self.admitted):
+        L = binding.lib()
+        n = ctypes.c_int()
+        while True:
+            binding._check(L.nbldpc_server_poll(self._h, self._buf, self.POLL_BATCH, ctypes.byref(n)),
+                           "nbldpc_server_poll")
+            now = self.clock() if n.value else 0.0
+            for i in range(n.value):
+                req = self._ids.pop(self._buf[i])
+                self._tags.pop(req._tag, None)
+                req.t_done = now
+                done.append(req)
+            if n.value < self.POLL_BATCH:
                 break
-            self.waiting.popleft()
-            self.used += b
-            r.t_admit = now
-            self.admitted.append(r)
-        self.peak_used = max(self.peak_used, self.used)
-        # launch admitted requests on free streams
-        busy = {ln.stream for ln in self.inflight}
-        for s in range(self.streams):
-            if not self.admitted:
-                break
-            if s in busy:
-                continue
-            group = []
-            while self.admitted and len(group) < self.max_jobs:
-                group.append(self.admitted.popleft())
-            wb = self.ex.launch_bytes(group, self.mode == "plain")
-            if self.used + wb > self.budget and self.inflight:
-                for r in reversed(group):
-                    self.admitted.appendleft(r)
-                break
-            self.used += wb
-            self.peak_used = max(self.peak_used, self.used)
-            for r in group:
-                r.t_launch = now
-            token = self.ex.start(group, s, self.mode == "plain")
-            self.inflight.append(_Launch(group, token, wb + sum(self.ex.request_bytes(r) for r in group), s))
-            # the request bytes were counted at admission; count them once
-            self.used -= sum(self.ex.request_bytes(r) for r in group)
-            self.launches += 1
-            busy.add(s)
         self.completed.extend(done)
         return done
 
+    def stats(self) -> binding.nbldpc_server_stats:
+        st = binding.nbldpc_server_stats()
+        binding._check(binding.lib().nbldpc_server_stats_get(self._h, ctypes.byref(st)), "nbldpc_server_stats_get")
+        return st
+
+    @property
+    def used(self) -> int:
+        return int(self.stats().used_bytes)
+
+    @property
+    def peak_used(self) -> int:
+        return int(self.stats().peak_bytes)
+
+    @property
+    def launches(self) -> int:
+        return int(self.stats().launches)
+
     def idle(self) -> bool:
-        return not (self.waiting or self.admitted or self.inflight)
+        st = self.stats()
+        return st.submitted == st.completed
 
     def drain(self, sleep: float = 0.0) -> None:
         while not self.idle():
@@ -162,71 +230,16 @@ class Server:
             if sleep:
                 time.sleep(sleep)
 
+    def close(self) -> None:
+        if self._h:
+            binding.lib().nbldpc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
-class CudaExecutor:
-    """Device work of the server: copies, nbldpc_decode_batch (or nbldpc_decode in plain mode), copies back."""
-
-    def __init__(self, decoders, max_iters: int, early_stop: int = 1, device="cuda", streams: int = 3):
-        from . import binding
-        self.b = binding
-        self.decs = decoders
-        self.max_iters = max_iters
-        self.early_stop = early_stop
-        self.dev = torch.device(device)
-        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(streams)]
-
-    def request_bytes(self, r: Request) -> int:
-        d = self.decs[r.code]
-        return r.frames * d.n * d.q + r.frames * (d.n + 5)
-
-    def _jobs(self, reqs, bufs):
-        return [(self.decs[r.code].handle, g, r.frames, self.max_iters, self.early_stop, s, i, o)
-                for r, (g, s, i, o) in zip(reqs, bufs)]
-
-    def launch_bytes(self, reqs, plain: bool = False) -> int:
-        if plain:
-            return sum(self.b.nbldpc_decode_workspace_size(self.decs[r.code].handle, r.frames) for r in reqs)
-        jobs = [(self.decs[r.code].handle, 0, r.frames, self.max_iters, self.early_stop, 0, 0, 0) for r in reqs]
-        return self.b.nbldpc_decode_batch_workspace_size(jobs)
-
-    def start(self, reqs, stream_index: int, plain: bool):
-        st = self.streams[stream_index % len(self.streams)]
-        bufs = []
-        with torch.cuda.stream(st):
-            for r in reqs:
-                d = self.decs[r.code]
-                g = torch.empty(r.gamma.shape, dtype=torch.uint8, device=self.dev)
-                g.copy_(r.gamma, non_blocking=True)
-                bufs.append((g, torch.empty((r.frames, d.n), dtype=torch.uint8, device=self.dev),
-                             torch.empty((r.frames,), dtype=torch.int32, device=self.dev),
-                             torch.empty((r.frames,), dtype=torch.uint8, device=self.dev)))
-            if plain:
-                (r,), ((g, s, i, o),) = reqs, bufs
-                d = self.decs[r.code]
-                ws = torch.empty(self.b.nbldpc_decode_workspace_size(d.handle, r.frames), dtype=torch.uint8,
-                                 device=self.dev)
-                self.b.nbldpc_decode(d.handle, g, r.frames, self.max_iters, 0, s, i, o, ws, stream=st)
-            else:
-                jobs = self._jobs(reqs, bufs)
-                ws = torch.empty(self.b.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8,
-                                 device=self.dev)
-                self.b.nbldpc_decode_batch(jobs, ws, stream=st)
-            for r, (g, s, i, o) in zip(reqs, bufs):
-                r.sym = torch.empty(s.shape, dtype=torch.uint8, pin_memory=True)
-                r.iters = torch.empty(i.shape, dtype=torch.int32, pin_memory=True)
-                r.ok = torch.empty(o.shape, dtype=torch.uint8, pin_memory=True)
-                r.sym.copy_(s, non_blocking=True)
-                r.iters.copy_(i, non_blocking=True)
-                r.ok.copy_(o, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(st)
-        return (ev, bufs, ws)
-
-    def done(self, token) -> bool:
-        return token[0].query()
-
-    def finish(self, token) -> None:
-        token[0].synchronize()
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 def percentile(xs, p: float) -> float:

@@ -102,3 +102,17 @@ def test_cnp_schedule_arguments_are_checked(lib):
     assert L.nbldpc_code_set_cnp_schedule(None, lib.NBLDPC_CNP_MINIMAL) == lib.NBLDPC_ERR_ARG
     s = ctypes.c_int()
     assert L.nbldpc_code_get_cnp_schedule(None, ctypes.byref(s)) == lib.NBLDPC_ERR_ARG
+
+
+def test_server_arguments_are_checked(lib):
+    L = lib.lib()
+    h = ctypes.c_void_p()
+    assert L.nbldpc_server_create_custom(None, 1 << 20, 2, 4, 0, ctypes.byref(h)) == lib.NBLDPC_ERR_ARG
+    ex = lib.nbldpc_server_executor()          # no callbacks
+    assert L.nbldpc_server_create_custom(ctypes.byref(ex), 1 << 20, 2, 4, 0, ctypes.byref(h)) == lib.NBLDPC_ERR_ARG
+    assert not h.value
+    n = ctypes.c_int()
+    assert L.nbldpc_server_poll(None, None, 0, ctypes.byref(n)) == lib.NBLDPC_ERR_ARG
+    st = lib.nbldpc_server_stats()
+    assert L.nbldpc_server_stats_get(None, ctypes.byref(st)) == lib.NBLDPC_ERR_ARG
+    L.nbldpc_server_destroy(None)

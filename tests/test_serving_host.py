@@ -7,12 +7,14 @@ from paper_2508_03567_gb300.serving import Request, Server, percentile
 
 
 class FakeExecutor:
-    """Completes a launch after `delay` polls; records what it was asked to do."""
+    """Completes a launch after `delay` polls; records what it was asked to do and which launches are
+    outstanding (started, not finished) with their stream and resident bytes."""
 
     def __init__(self, req_bytes=100, ws_bytes=50, delay=2):
         self.req_bytes, self.ws_bytes, self.delay = req_bytes, ws_bytes, delay
         self.starts = []
         self.polls = {}
+        self.active = {}
 
     def request_bytes(self, r):
         return self.req_bytes * r.frames
@@ -24,6 +26,7 @@ class FakeExecutor:
         tok = len(self.starts)
         self.starts.append(([r.rid for r in reqs], stream, plain))
         self.polls[tok] = 0
+        self.active[tok] = (stream, self.ws_bytes + sum(self.request_bytes(r) for r in reqs))
         for r in reqs:
             r.sym = torch.zeros((r.frames, 1), dtype=torch.uint8)
         return tok
@@ -33,7 +36,7 @@ class FakeExecutor:
         return self.polls[tok] > self.delay
 
     def finish(self, tok):
-        pass
+        del self.active[tok]
 
 
 def req(i, frames=1):
@@ -56,14 +59,17 @@ def test_budget_is_never_exceeded_and_order_is_kept():
     for i in range(60):
         srv.submit(req(i, int(rng.integers(1, 4))))
         srv.poll()
-        assert srv.used <= srv.budget
+        # the accounted bytes cover every launch in flight (its workspace and its requests) and
+        # never pass the budget
+        assert sum(b for _, b in ex.active.values()) <= srv.used <= srv.budget
     srv.drain()
     assert srv.peak_used <= srv.budget
+    assert srv.used == 0 and not ex.active                   # everything released
     launched = [rid for rids, _, _ in ex.starts for rid in rids]
     assert launched == list(range(60))                       # arrival order
     assert all(len(rids) <= 4 for rids, _, _ in ex.starts)   # group size limit
     assert sorted(r.rid for r in srv.completed) == list(range(60))
-    assert all(r.t_arrival <= r.t_admit <= r.t_launch <= r.t_done for r in srv.completed)
+    assert all(r.t_arrival <= r.t_launch <= r.t_done for r in srv.completed)
 
 
 def test_streams_are_not_oversubscribed():
@@ -73,8 +79,8 @@ def test_streams_are_not_oversubscribed():
         srv.submit(req(i))
     for _ in range(200):
         srv.poll()
-        assert len(srv.inflight) <= 3
-        assert len({ln.stream for ln in srv.inflight}) == len(srv.inflight)
+        streams = [st for st, _ in ex.active.values()]
+        assert len(streams) <= 3 and len(set(streams)) == len(streams)
         if srv.idle():
             break
     assert srv.idle()
