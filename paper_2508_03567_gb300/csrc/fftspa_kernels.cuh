@@ -15,7 +15,8 @@
 //     W(s) = sum_x (-1)^popcount(s & x) u(x),
 // whose inverse is the same transform divided by q.  A check vector is spread
 // over G lanes of R elements each (element y = lane * R + r): butterflies on
-// the bits of r run in registers, those on the lane bits through shuffles.
+// the bits of r run in registers, those on the lane bits through half
+// exchanges between partner lanes (one shuffle per two butterfly inputs).
 //
 // Multiplication by a field constant is linear over GF(2), so the permuted
 // index h^-1 (y0 ^ r) of a lane's R elements is h^-1 y0 ^ h^-1 r, and
@@ -79,11 +80,10 @@ template <int Q, int DV> struct VnpGeo {
   static constexpr int VG = Q / RV;
 };
 
-// Walsh-Hadamard butterflies over the R register elements (index bits
-// 0..RB-1) then the G lanes of the group (bits RB..p-1): the pair
-// (a, b) at indices (x, x + 2^k) becomes (a + b, a - b).
+// Walsh-Hadamard butterflies over the R register elements: the pair (a, b)
+// at register indices (r, r + h) becomes (a + b, a - b).
 template <class g>
-__device__ __forceinline__ void wht(float (&v)[g::R], int gl, unsigned gmask) {
+__device__ __forceinline__ void wht_regs(float (&v)[g::R]) {
 #pragma unroll
   for (int h = 1; h < g::R; h <<= 1) {
 #pragma unroll
@@ -95,14 +95,74 @@ __device__ __forceinline__ void wht(float (&v)[g::R], int gl, unsigned gmask) {
       }
     }
   }
+}
+
+// Butterfly over lane bit k by half exchanges: the lanes of a pair (gl, gl ^ 2^k)
+// hold the same register indices of the two elements of each butterfly; the
+// lower lane keeps registers with bit c = 2^(k mod RB) clear and sends the
+// others, the upper lane the reverse, so one shuffle moves two butterfly
+// inputs and each lane then computes both outputs of the butterflies it
+// holds: low = keep + recv (a + b), high = +-(keep - recv) (a - b, exact).
+// Afterwards register bit c carries the element's lane bit k and lane bit k the
+// element's register bit c; applying the stages k = 0..K-1 and later
+// K-1..0 restores the layout (the products between the transforms are
+// element-wise, so they see the same layout for every edge).
+template <class g>
+__device__ __forceinline__ void lane_stage(float (&v)[g::R], int k, int gl, unsigned gmask) {
+  const int o = 1 << k;
+  const int c = 1 << (k % g::RB);
+  const bool up = (gl & o) != 0;
+  const float sg = up ? -1.f : 1.f;
 #pragma unroll
-  for (int o = 1; o < g::G; o <<= 1) {
-    const float sg = (gl & o) ? -1.f : 1.f;   // upper index: partner - own
+  for (int r = 0; r < g::R; ++r) {
+    if (r & c) continue;
+    const float send = up ? v[r] : v[r | c];
+    const float keep = up ? v[r | c] : v[r];
+    const float recv = __shfl_xor_sync(gmask, send, o);
+    v[r] = keep + recv;
+    v[r | c] = sg * (keep - recv);
+  }
+}
+
+// Butterfly over lane bit k with every element shuffled: the upper lane of
+// the pair computes partner - own, the lower own + partner (layout unchanged).
+// Used for q >= 128, where the selects of the half exchange cost more than
+// the shuffles they save (measured on GB300: GF(256) -8 % with half
+// exchanges; GF(16) +7 %, GF(8) / GF(64) +1 %, GF(32) -1 %).
+template <class g>
+__device__ __forceinline__ void lane_stage_full(float (&v)[g::R], int k, int gl, unsigned gmask) {
+  const int o = 1 << k;
+  const float sg = (gl & o) ? -1.f : 1.f;
 #pragma unroll
-    for (int r = 0; r < g::R; ++r) {
-      const float t = __shfl_xor_sync(gmask, v[r], o);
-      v[r] = fmaf(sg, v[r], t);
-    }
+  for (int r = 0; r < g::R; ++r) {
+    const float t = __shfl_xor_sync(gmask, v[r], o);
+    v[r] = fmaf(sg, v[r], t);
+  }
+}
+
+template <class g> struct HalfExchange { static constexpr bool v = g::Q <= 64; };
+
+// forward transform: register bits, then lane bits 0..K-1 (natural layout in,
+// exchanged layout out)
+template <class g>
+__device__ __forceinline__ void wht_fwd(float (&v)[g::R], int gl, unsigned gmask) {
+  wht_regs<g>(v);
+#pragma unroll
+  for (int k = 0; (1 << k) < g::G; ++k) {
+    if constexpr (HalfExchange<g>::v) lane_stage<g>(v, k, gl, gmask);
+    else lane_stage_full<g>(v, k, gl, gmask);
+  }
+}
+
+// inverse (unnormalized) transform: register bits, then lane bits K-1..0
+// (exchanged layout in, natural layout out)
+template <class g>
+__device__ __forceinline__ void wht_inv(float (&v)[g::R], int gl, unsigned gmask) {
+  wht_regs<g>(v);
+#pragma unroll
+  for (int k = g::LQ - g::RB - 1; k >= 0; --k) {
+    if constexpr (HalfExchange<g>::v) lane_stage<g>(v, k, gl, gmask);
+    else lane_stage_full<g>(v, k, gl, gmask);
   }
 }
 
@@ -422,7 +482,7 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
           const float* src = first ? pf + (size_t)edge_col[e] * Q : X + (size_t)e * Q;
 #pragma unroll
           for (int i = 0; i < R; ++i) W[j][i] = src[idx[i]];
-          wht<g>(W[j], gl, gmask);
+          wht_fwd<g>(W[j], gl, gmask);
         } else {
 #pragma unroll
           for (int i = 0; i < R; ++i) W[j][i] = 1.f;   // transform of the unit vector at 0
@@ -440,7 +500,7 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
               if (k != j) t *= W[k][i];
             v[i] = t;
           }
-          wht<g>(v, gl, gmask);
+          wht_inv<g>(v, gl, gmask);
           const int e = e0 + j;
           int idx[R];
           perm_index<g>(idx, exp2, edge_lhi[e], ly0, y0nz);
