@@ -794,6 +794,7 @@ def main():
     info_bits_step = frames * code.k * code.p
     value = ws * args.steps * info_bits_step / total_s / 1e6
     kernel_s = statistics.mean(step_ms) / 1e3
+    median_ms = statistics.median(step_ms)
     achieved_gops = 2 * pairs_step / kernel_s / 1e9           # 16-bit min/max ops per second
     clocks = clk.summary()
     mhz, mhz_kind = sm_max_mhz()
@@ -831,7 +832,10 @@ def main():
         "cpu_baseline": cpu,
         "decode_stats": {"mean_iters": float(its_h.mean()), "fer_proxy_not_ok": float(1 - ok_h.mean()),
                          "pairs_per_step": pairs_step, "kernel_ms": 1e3 * kernel_s,
+                         "median_ms_per_step": median_ms,
                          "wall_ms_per_step": 1e3 * (t1 - t0) / args.steps},
+        # the paper's throughput formula counts coded bits (N p per frame)
+        "coded_mbps": value * code.n / code.k,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -863,10 +867,22 @@ def measure_e2e(binding, dec, code, gamma_dev, mi, es, args, dev):
     for _ in range(steps):
         step()
     dt = (time.perf_counter() - t0) / steps
+    # the host-to-device copy of the step's reliabilities alone (the paper times transfers apart)
+    dst = torch.empty(gamma_dev.shape, dtype=torch.uint8, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        dst.copy_(g_host, non_blocking=True)
+        a.record(stream)
+        dst.copy_(g_host, non_blocking=True)
+        b.record(stream)
+    stream.synchronize()
+    h2d_ms = a.elapsed_time(b)
+    del dst
     bits = frames * code.k * code.p
     return {"value": bits / dt / 1e6, "unit": "Mbit/s", "h2d_bytes_per_step": int(g_host.numel()),
             "d2h_bytes_per_step": int(sym.numel() + 4 * its.numel() + ok.numel()),
-            "ms_per_step": 1e3 * dt, "steps": steps, "chunk_frames": chunk}
+            "ms_per_step": 1e3 * dt, "steps": steps, "chunk_frames": chunk,
+            "h2d_only_ms_per_step": h2d_ms, "h2d_only_gbs": g_host.numel() / h2d_ms / 1e6}
 
 
 if __name__ == "__main__":
