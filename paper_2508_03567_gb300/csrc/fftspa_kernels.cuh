@@ -13,10 +13,14 @@
 //
 // The transform over (Z_2)^p is the radix-2 Walsh-Hadamard transform,
 //     W(s) = sum_x (-1)^popcount(s & x) u(x),
-// whose inverse is the same transform divided by q.  A check vector is spread
-// over G lanes of R elements each (element y = lane * R + r): butterflies on
-// the bits of r run in registers, those on the lane bits through half
-// exchanges between partner lanes (one shuffle per two butterfly inputs).
+// whose inverse is the same transform divided by q.  The check-node pass has
+// two forms.  Distributed (q >= 8, check degree <= 8): a check vector is
+// spread over G lanes of R elements each (element y = lane * R + r);
+// butterflies on the bits of r run in registers, those on the lane bits
+// through half exchanges between partner lanes (q <= 64: one shuffle per two
+// butterfly inputs) or one shuffle per element (q >= 128).  Lane per edge
+// (q <= 4, or a check of degree 9..32): one lane holds a whole vector and the
+// permutation moves into the transform domain (see cnp_lane).
 //
 // Multiplication by a field constant is linear over GF(2), so the permuted
 // index h^-1 (y0 ^ r) of a lane's R elements is h^-1 y0 ^ h^-1 r, and
