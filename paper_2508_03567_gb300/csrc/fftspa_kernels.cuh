@@ -55,21 +55,30 @@ struct FftParams {
 };
 
 // Elements per lane and block size of the distributed check-node form at
-// q = 64 (compile-time tuning knobs; the defaults are the measured best on
-// GB300, GF(64) (2,4) N=576: 4 elements / 768 threads 1.19 Gbit/s, 8 / 768
-// 0.97, 16 / 512 0.72, 2 / 1024 1.05, 4 / 896 1.08).
+// q = 64 and q = 128, and the largest q with half-exchange lane stages
+// (compile-time tuning knobs; the defaults are the measured best on GB300:
+// GF(64) (2,4) N=576: 4 elements / 768 threads 1.19 Gbit/s, 8 / 768 0.97,
+// 16 / 512 0.72, 2 / 1024 1.05, 4 / 896 1.08; GF(128) (2,4) N=256: 4
+// elements 0.81, 8 elements 0.71).
 #ifndef NBLDPC_FFT_R64
 #define NBLDPC_FFT_R64 4
 #endif
 #ifndef NBLDPC_FFT_T64
 #define NBLDPC_FFT_T64 768
 #endif
+#ifndef NBLDPC_FFT_R128
+#define NBLDPC_FFT_R128 4
+#endif
+#ifndef NBLDPC_FFT_HALF_MAXQ
+#define NBLDPC_FFT_HALF_MAXQ 64
+#endif
 
 template <int Q_> struct FftGeo {
   static constexpr int Q = Q_;
   static constexpr int LQ = ilog2(Q);                 // p
   static constexpr int PB = LQ > 0 ? LQ : 1;          // basis images per coefficient
-  static constexpr int R = Q < 8 ? (Q < 4 ? Q : 4) : (Q <= 64 ? NBLDPC_FFT_R64 : 8);   // check-vector elements per lane
+  static constexpr int R = Q < 8 ? (Q < 4 ? Q : 4)
+                                  : (Q <= 64 ? NBLDPC_FFT_R64 : (Q == 128 ? NBLDPC_FFT_R128 : 8));   // elements per lane
   static constexpr int RB = ilog2(R);
   static constexpr int G = Q / R;                     // lanes per check vector (1..32)
 };
@@ -144,7 +153,7 @@ __device__ __forceinline__ void lane_stage_full(float (&v)[g::R], int k, int gl,
   }
 }
 
-template <class g> struct HalfExchange { static constexpr bool v = g::Q <= 64; };
+template <class g> struct HalfExchange { static constexpr bool v = g::Q <= NBLDPC_FFT_HALF_MAXQ; };
 
 // forward transform: register bits, then lane bits 0..K-1 (natural layout in,
 // exchanged layout out)
