@@ -116,12 +116,18 @@ template <int Q_, int V_> struct Geo {
 
 // Of the XN * AWN maxima of one shuffle step, FmaEighths eighths use
 // vmax2_fma (the rest the ALU pipe, which also takes every minimum).  Measured
-// on GB300: 3/8 is best for q <= 64; for q >= 128 the ALU pipe is not the
-// limit and the extra issue slots of the FMA form cost throughput.
+// on GB300: 3/8 is best for q <= 64 (GF(64) step: 5/16 435.6, 6/16 437.5,
+// 7/16 434.9, 8/16 430.4 Mbit/s); 1/8 for q >= 128 (four-code batch, 90 % of
+// its work in GF(256): 0 89.5, 1/8 91.5, 2/8 87.7, 3/8 83.2 Mbit/s).
 #ifndef NBLDPC_FMA_EIGHTHS
 #define NBLDPC_FMA_EIGHTHS 3
 #endif
-template <int Q> struct FmaEighths { static constexpr int v = Q >= 128 ? 0 : NBLDPC_FMA_EIGHTHS; };
+#ifndef NBLDPC_FMA_EIGHTHS_WIDE
+#define NBLDPC_FMA_EIGHTHS_WIDE 1
+#endif
+template <int Q> struct FmaEighths {
+  static constexpr int v = Q >= 128 ? NBLDPC_FMA_EIGHTHS_WIDE : NBLDPC_FMA_EIGHTHS;
+};
 template <class g> struct FmaMax { static constexpr int v = (g::XN * g::AWN * FmaEighths<g::Q>::v) / 8; };
 
 // Lane constants of the convolution, computed once per thread.
