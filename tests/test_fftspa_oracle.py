@@ -227,3 +227,31 @@ def test_fftspa_corrects_more_than_it_starts_with(oracle_lib):
     sym, its, ok = oracle_lib.fftspa_decode(code, p, 20, 1)
     cw = b.codewords.numpy()
     assert (sym != cw).sum() < (np.argmax(p, -1) != cw).sum()
+
+
+def test_normalization_fallback_gives_uniform_vectors(oracle_lib):
+    """A frame whose probabilities are all zero: every normalization sum is 0, so every message
+    and a-posteriori vector is the uniform 1/q (the reading for non-positive sums), and the
+    decision is symbol 0 (lowest symbol on ties)."""
+    code = I.workload_code("gf4_n48_dv2_dc4")
+    p = np.zeros((1, code.n, code.q), np.float32)
+    sym, its, ok, app = oracle_lib.fftspa_decode(code, p, 3, 0, want_app=True)
+    np.testing.assert_allclose(app, 1.0 / code.q, atol=0)
+    assert np.all(sym == 0) and ok[0] == 1 and its[0] == 3      # the all-zero word is a codeword
+
+
+def test_channel_probabilities_match_the_reliabilities():
+    """Both inputs come from the same noise: the most likely symbol of p is the symbol with
+    gamma = 0 (the hard decision), p sums to 1, and p falls as gamma grows."""
+    code = I.workload_code("gf16_n1024_dv2_dc4")
+    b = I.make_batch(code, 2.0, 123, 4, prob=True)
+    p, g = b.prob.numpy().astype(np.float64), b.gamma.numpy()
+    np.testing.assert_allclose(p.sum(-1), 1.0, atol=1e-5)
+    assert np.all(g[np.arange(4)[:, None], np.arange(code.n)[None, :], np.argmax(p, -1)] == 0)
+    # within a symbol, a strictly larger unsaturated gamma never has a larger probability
+    for f in range(2):
+        for n in range(0, code.n, 97):
+            order = np.argsort(g[f, n], kind="stable")
+            gs, ps = g[f, n][order], p[f, n][order]
+            keep = gs < 63
+            assert np.all(np.diff(ps[keep])[np.diff(gs[keep]) > 0] <= 1e-7)
