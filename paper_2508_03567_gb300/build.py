@@ -40,6 +40,7 @@ def _units():
     units = [(os.path.join(CSRC, "kernels.cu"), f"kernels_q{q}.o", [f"-DNBLDPC_KQ={q}"]) for q in KERNEL_UNITS]
     units += [(os.path.join(CSRC, "fftspa.cu"), f"fftspa_q{q}.o", [f"-DNBLDPC_FQ={q}"]) for q in FFT_UNITS]
     units.append((os.path.join(CSRC, "nbldpc.cu"), "nbldpc.o", []))
+    units.append((os.path.join(CSRC, "fftspa_host.cu"), "fftspa_host.o", []))
     units.append((os.path.join(CSRC, "server.cu"), "server.o", []))
     return units
 

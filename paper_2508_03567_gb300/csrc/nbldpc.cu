@@ -1,69 +1,29 @@
-// C ABI of the GB300 min-max NB-LDPC decoder (declarations and contracts in
-// include/nbldpc.h).  Host side: argument validation, GF tables, code upload,
-// launch planning, the autotuner and stream-ordered launches of the decode
-// kernel.
+// C ABI of the GB300 NB-LDPC decoders (declarations and contracts in
+// include/nbldpc.h), min-max side: argument validation, GF tables, code upload
+// (with the FFT-SPA blob section), launch planning, mixed batches, the
+// autotuner, host-buffer and non-allocating decodes, stream-ordered launches
+// of the min-max kernels.  FFT-SPA decodes are in fftspa_host.cu.
 #include "nbldpc.h"
 
-#include <atomic>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
-#include "fftspa_kernels.cuh"
+#include "host_internal.h"
 #include "mma_kernels.cuh"
 
 static_assert(nbldpc::kMaxJobs == NBLDPC_MAX_BATCH_JOBS, "job table size");
 static_assert(sizeof(nbldpc::LaunchParams) < 32000, "kernel parameter space");
-static_assert(sizeof(nbldpc::FftParams) < 4000, "kernel parameter space");
 
-namespace {
+std::atomic<uint64_t> nbldpc_host::g_launches{0};
+std::mutex nbldpc_host::g_attr_mu;
 
-std::atomic<uint64_t> g_launches{0};
-
-// Launch shape of one kernel for one set of codes.
-struct Plan {
-  int fpb = 1;          // frame slots per block
-  int threads = 256;    // block size
-  int slot_smem = 0;    // shared bytes per frame slot
-  int smem = 0;         // shared bytes per block
-  int per_sm = 0;       // resident blocks per SM
-  int grid_max = 0;     // resident blocks on the device
-  int blob_cap = 0, n_cap = 0;
-  size_t slot_bytes = 0;  // message slot per frame slot
-};
-
-}  // namespace
-
-struct nbldpc_code {
-  int q = 0, p = 0, n = 0, m = 0, nnz = 0, dmax = 0, vmax = 0;
-  uint32_t poly = 0;
-  int device = 0;
-  unsigned char* blob_dev = nullptr;
-  nbldpc::CodeBlob off{};
-  int variant = 0;                     // layout variant used by every decode of this code
-  int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
-  int cnp_schedule = NBLDPC_CNP_MINIMAL;   // check-node convolutions: 3(d-2) or Table 1's 3d-4
-  Plan plan{};                         // single-code launch shape (fpb chosen by default or by the autotuner)
-  int fft_status = NBLDPC_ERR_UNSUPPORTED;   // FFT-SPA launch shape below valid when NBLDPC_OK
-  int fft_dc = 0, fft_dv = 0;          // degree buckets of the FFT-SPA kernel (dc 0: q <= 64 lane-per-edge path)
-  int ntasks = 0;                      // FFT-SPA warp tasks (blob section)
-  Plan fft_plan{};
-  std::mutex mu;                       // guards the lazily created copy stream
-  cudaStream_t side = nullptr;         // second stream for nbldpc_decode_host
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-};
+using namespace nbldpc_host;
 
 namespace {
 
 constexpr int kThreads = 256;
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? NBLDPC_OK : NBLDPC_ERR_CUDA; }
-
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Field tables by repeated multiplication by x modulo the primitive
 // polynomial; fails unless x generates all q-1 non-zero elements.
@@ -100,14 +60,6 @@ const void* kernel_q32(int v, int mb, int t1);
 const void* kernel_q64(int v, int mb, int t1);
 const void* kernel_q128(int v, int mb, int t1);
 const void* kernel_q256(int v, int mb, int t1);
-const void* fft_kernel_q2(int dc, int dv, int* threads);
-const void* fft_kernel_q4(int dc, int dv, int* threads);
-const void* fft_kernel_q8(int dc, int dv, int* threads);
-const void* fft_kernel_q16(int dc, int dv, int* threads);
-const void* fft_kernel_q32(int dc, int dv, int* threads);
-const void* fft_kernel_q64(int dc, int dv, int* threads);
-const void* fft_kernel_q128(int dc, int dv, int* threads);
-const void* fft_kernel_q256(int dc, int dv, int* threads);
 }  // namespace nbldpc
 
 namespace {
@@ -166,7 +118,6 @@ int group_bytes(int q, int dmax, int mb) {
 
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
-std::mutex g_attr_mu;
 bool g_attr_done[64][49] = {};
 
 int kernel_slot(int q, int v, int km) {
@@ -259,13 +210,6 @@ int configure(nbldpc_code* c, int variant, int fpb) {
   return NBLDPC_OK;
 }
 
-int grid_for(const Plan& pl, int frames) {
-  const int want = (frames + pl.fpb - 1) / pl.fpb;
-  return want < pl.grid_max ? want : pl.grid_max;
-}
-
-size_t ws_bytes(const Plan& pl, int frames) { return 256 + (size_t)grid_for(pl, frames) * pl.fpb * pl.slot_bytes; }
-
 size_t decode_ws_bytes(const nbldpc_code* c, int frames) { return ws_bytes(c->plan, frames); }
 
 nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
@@ -320,175 +264,6 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
   lp.total_items = frames;
   return launch_plan(kernel_for(c->q, c->variant, kmode(c)), c->plan, lp, grid_for(c->plan, frames), ws,
                      reinterpret_cast<uint8_t*>(ws) + 256, st);
-}
-
-// ---- FFT-SPA (Alg. 1) --------------------------------------------------------
-const void* fft_kernel_for(int q, int dc, int dv, int* threads = nullptr) {
-  switch (q) {
-    case 2: return nbldpc::fft_kernel_q2(dc, dv, threads);
-    case 4: return nbldpc::fft_kernel_q4(dc, dv, threads);
-    case 8: return nbldpc::fft_kernel_q8(dc, dv, threads);
-    case 16: return nbldpc::fft_kernel_q16(dc, dv, threads);
-    case 32: return nbldpc::fft_kernel_q32(dc, dv, threads);
-    case 64: return nbldpc::fft_kernel_q64(dc, dv, threads);
-    case 128: return nbldpc::fft_kernel_q128(dc, dv, threads);
-    case 256: return nbldpc::fft_kernel_q256(dc, dv, threads);
-  }
-  return nullptr;
-}
-
-// Largest field order whose codes take the lane-per-edge check-node form at
-// every check degree (compile-time tuning knob).  Measured on GB300 (Mbit/s,
-// lane per edge against distributed with 4 elements per lane): GF(4) (2,4)
-// N=48 1336 vs 1117, GF(8) (2,4) N=512 1441 vs 1467, GF(16) (2,4) N=1024
-// 1432 vs 1759, GF(32) (3,6) N=600 408 vs 588.
-#ifndef NBLDPC_FFT_LANE_MAXQ
-#define NBLDPC_FFT_LANE_MAXQ 4
-#endif
-
-bool g_fft_attr_done[64][8][3][3] = {};   // device, log2(q) - 1, check-node form, column-degree bucket
-
-// Launch shape of the FFT-SPA kernel for a code: degree buckets (check
-// degree <= 4 or 8, column degree <= 2, 4 or 8), block size (one frame per
-// SM), shared memory (code blob, decisions, control word), resident blocks,
-// message slot of nnz * q floats.
-int fft_configure(nbldpc_code* c) {
-  // check-node form: lane per edge (dc 0: check degree <= 32) for small fields
-  // and for q <= 64 codes with a check of degree > 8; otherwise the
-  // distributed form with the check degree bucket 4 or 8
-  const bool lane_form = c->q <= NBLDPC_FFT_LANE_MAXQ || (c->q <= 64 && c->dmax > 8);
-  const int dc = lane_form ? (c->dmax <= 32 ? 0 : -1) : (c->dmax <= 4 ? 4 : (c->dmax <= 8 ? 8 : -1));
-  const int dv = c->vmax <= 2 ? 2 : (c->vmax <= 4 ? 4 : (c->vmax <= 8 ? 8 : 0));
-  if (dc < 0 || !dv) return NBLDPC_ERR_UNSUPPORTED;
-  int threads = 0;
-  const void* k = fft_kernel_for(c->q, dc, dv, &threads);
-  if (!k) return NBLDPC_ERR_UNSUPPORTED;
-  int dev = 0, sms = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
-  if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
-  Plan pl{};
-  pl.fpb = 1;
-  pl.threads = threads;
-  pl.blob_cap = (int)round_up((size_t)c->off.fft_bytes, 16);
-  pl.n_cap = (int)round_up((size_t)c->n, 16);
-  const int w_area = dc == 0 ? threads * c->q * (int)sizeof(float) : 0;   // one transformed vector per lane
-  pl.slot_smem = pl.smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16), 256) + w_area;
-  if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
-  {
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    bool& done = g_fft_attr_done[dev][nbldpc::ilog2(c->q) - 1][dc == 0 ? 0 : (dc == 4 ? 1 : 2)][dv == 2 ? 0 : (dv == 4 ? 1 : 2)];
-    if (!done) {
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
-        return NBLDPC_ERR_CUDA;
-      done = true;
-    }
-  }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, k, pl.threads, pl.smem) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
-  if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
-  pl.grid_max = pl.per_sm * sms;
-  pl.slot_bytes = round_up((size_t)c->nnz * c->q * sizeof(float), 256);
-  c->fft_plan = pl;
-  c->fft_dc = dc;
-  c->fft_dv = dv;
-  return NBLDPC_OK;
-}
-
-int fft_launch(const nbldpc_code* c, const float* prob, int frames, int max_iters, int early_stop, uint8_t* sym,
-               int32_t* iters, uint8_t* ok, float* app, void* ws, cudaStream_t st) {
-  const Plan& pl = c->fft_plan;
-  nbldpc::FftParams fp{};
-  fp.job.blob = c->blob_dev;
-  fp.job.off = c->off;
-  fp.job.prob = prob;
-  fp.job.out_sym = sym;
-  fp.job.out_iters = iters;
-  fp.job.out_ok = ok;
-  fp.job.out_app = app;
-  fp.job.q = c->q;
-  fp.job.n = c->n;
-  fp.job.m = c->m;
-  fp.job.frames = frames;
-  fp.job.max_iters = max_iters;
-  fp.job.early_stop = early_stop ? 1 : 0;
-  fp.counter = reinterpret_cast<unsigned int*>(ws);
-  fp.msg = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ws) + 256);
-  fp.slot_floats = pl.slot_bytes / sizeof(float);
-  fp.blob_cap = pl.blob_cap;
-  fp.n_cap = pl.n_cap;
-  fp.w_off = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16), 256);
-  fp.job.ntasks = c->ntasks;
-  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  void* args[] = {&fp};
-  e = cudaLaunchKernel(fft_kernel_for(c->q, c->fft_dc, c->fft_dv), dim3(grid_for(pl, frames)), dim3(pl.threads),
-                       args, (size_t)pl.smem, st);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  return NBLDPC_OK;
-}
-
-// ---- host-buffer decodes (nbldpc_decode_host, nbldpc_fftspa_decode_host) ------
-// One chunk's device buffers: input rows, symbols, iterations, ok flags, decoder workspace.
-size_t host_chunk_bytes(const nbldpc_code* c, int chunk_frames, size_t in_bytes_per_frame, size_t decode_ws) {
-  return round_up((size_t)chunk_frames * in_bytes_per_frame, 256) + round_up((size_t)chunk_frames * c->n, 256) +
-         round_up((size_t)chunk_frames * 4, 256) + round_up((size_t)chunk_frames, 256) + round_up(decode_ws, 256);
-}
-
-// Decode host rows in chunks: chunk i copies its rows in, decodes and copies its
-// outputs back on stream i % 2 (the caller's stream or the code's side stream),
-// in buffer half i % 2 of the workspace, so one chunk's copies overlap the other's
-// decode.  `per` is one half's size; `dec` queues the decode of one chunk.
-template <class Dec>
-int host_chunks(nbldpc_code* c, const void* in_host, size_t fbytes, int frames, uint8_t* out_sym_host,
-                int32_t* out_iters_host, uint8_t* out_ok_host, int chunk_frames, void* workspace_dev,
-                size_t workspace_bytes, size_t per, void* cuda_stream, Dec dec) {
-  if (!in_host || !out_sym_host || !out_iters_host || !out_ok_host || !workspace_dev) return NBLDPC_ERR_ARG;
-  if (!aligned(workspace_dev, 256) || workspace_bytes < 2 * per) return NBLDPC_ERR_ARG;
-  int st = cuda_status(cudaGetLastError());
-  if (st != NBLDPC_OK) return st;
-  cudaStream_t main = reinterpret_cast<cudaStream_t>(cuda_stream);
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    if (!c->side) {
-      if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) return NBLDPC_ERR_CUDA;
-      for (auto& ev : c->ev)
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return NBLDPC_ERR_CUDA;
-    }
-  }
-  std::lock_guard<std::mutex> lk(c->mu);  // one host decode at a time per handle (shared side stream)
-  const size_t g_b = round_up((size_t)chunk_frames * fbytes, 256), s_b = round_up((size_t)chunk_frames * c->n, 256),
-               i_b = round_up((size_t)chunk_frames * 4, 256), o_b = round_up((size_t)chunk_frames, 256);
-  cudaStream_t streams[2] = {main, c->side};
-  // the side stream starts after work already queued on the caller's stream
-  if (cudaEventRecord(c->ev[0], main) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev[0], 0) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
-  const unsigned char* src = reinterpret_cast<const unsigned char*>(in_host);
-  for (int f0 = 0, i = 0; f0 < frames; f0 += chunk_frames, ++i) {
-    const int nf = frames - f0 < chunk_frames ? frames - f0 : chunk_frames;
-    unsigned char* base = reinterpret_cast<unsigned char*>(workspace_dev) + (size_t)(i & 1) * per;
-    void* g = base;
-    uint8_t* sy = base + g_b;
-    int32_t* it = reinterpret_cast<int32_t*>(base + g_b + s_b);
-    uint8_t* okb = base + g_b + s_b + i_b;
-    void* ws = base + g_b + s_b + i_b + o_b;
-    cudaStream_t s = streams[i & 1];
-    cudaError_t e = cudaMemcpyAsync(g, src + (size_t)f0 * fbytes, (size_t)nf * fbytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-    st = dec(g, nf, sy, it, okb, ws, s);
-    if (st != NBLDPC_OK) return st;
-    e = cudaMemcpyAsync(out_sym_host + (size_t)f0 * c->n, sy, (size_t)nf * c->n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_iters_host + f0, it, (size_t)nf * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_ok_host + f0, okb, (size_t)nf, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
-  }
-  // the caller's stream completes only after the side stream's chunks
-  if (cudaEventRecord(c->ev[1], c->side) != cudaSuccess || cudaStreamWaitEvent(main, c->ev[1], 0) != cudaSuccess)
-    return NBLDPC_ERR_CUDA;
-  return NBLDPC_OK;
 }
 
 // ---- non-allocating decode (nbldpc_decode_noalloc) -------------------------
@@ -777,30 +552,6 @@ int nbldpc_decode(const nbldpc_code* c, const uint8_t* gamma_dev, int frames, in
                 workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
-// ---- FFT-SPA decoding ----------------------------------------------------------
-int nbldpc_fftspa_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
-  if (!c || frames < 0 || !bytes) return NBLDPC_ERR_ARG;
-  if (c->fft_status != NBLDPC_OK) return c->fft_status;
-  *bytes = ws_bytes(c->fft_plan, frames);
-  return NBLDPC_OK;
-}
-
-int nbldpc_fftspa_decode(const nbldpc_code* c, const float* prob_dev, int frames, int max_iters, int early_stop,
-                         uint8_t* out_sym_dev, int32_t* out_iters_dev, uint8_t* out_ok_dev, float* out_app_dev,
-                         void* workspace_dev, size_t workspace_bytes, void* cuda_stream) {
-  if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
-  if (c->fft_status != NBLDPC_OK) return c->fft_status;
-  if (frames == 0) return NBLDPC_OK;
-  if (!prob_dev || !out_sym_dev || !out_iters_dev || !out_ok_dev || !workspace_dev) return NBLDPC_ERR_ARG;
-  if (!aligned(prob_dev, 16) || !aligned(out_iters_dev, 4) || !aligned(workspace_dev, 16)) return NBLDPC_ERR_ARG;
-  if (out_app_dev && !aligned(out_app_dev, 16)) return NBLDPC_ERR_ARG;
-  if (workspace_bytes < ws_bytes(c->fft_plan, frames)) return NBLDPC_ERR_ARG;
-  int st = cuda_status(cudaGetLastError());
-  if (st != NBLDPC_OK) return st;
-  return fft_launch(c, prob_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, out_app_dev,
-                    workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
-}
-
 // ---- mixed-code batches -----------------------------------------------------
 static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) {
   if (!jobs || n_jobs < 1 || n_jobs > NBLDPC_MAX_BATCH_JOBS) return NBLDPC_ERR_ARG;
@@ -941,31 +692,6 @@ int nbldpc_decode_host(const nbldpc_code* cc, const uint8_t* gamma_host, int fra
                      [&](const void* in, int nf, uint8_t* sy, int32_t* it, uint8_t* okb, void* ws, cudaStream_t s) {
                        return launch(c, reinterpret_cast<const uint8_t*>(in), nf, max_iters, early_stop, sy, it, okb,
                                      ws, s);
-                     });
-}
-
-int nbldpc_fftspa_decode_host_workspace_size(const nbldpc_code* c, int chunk_frames, size_t* bytes) {
-  if (!c || !bytes || chunk_frames <= 0) return NBLDPC_ERR_ARG;
-  if (c->fft_status != NBLDPC_OK) return c->fft_status;
-  *bytes = 2 * host_chunk_bytes(c, chunk_frames, (size_t)c->n * c->q * sizeof(float),
-                                ws_bytes(c->fft_plan, chunk_frames));
-  return NBLDPC_OK;
-}
-
-int nbldpc_fftspa_decode_host(const nbldpc_code* cc, const float* prob_host, int frames, int max_iters,
-                              int early_stop, uint8_t* out_sym_host, int32_t* out_iters_host, uint8_t* out_ok_host,
-                              int chunk_frames, void* workspace_dev, size_t workspace_bytes, void* cuda_stream) {
-  nbldpc_code* c = const_cast<nbldpc_code*>(cc);
-  if (!c || frames < 0 || max_iters < 0 || chunk_frames <= 0) return NBLDPC_ERR_ARG;
-  if (c->fft_status != NBLDPC_OK) return c->fft_status;
-  if (frames == 0) return NBLDPC_OK;
-  const size_t fbytes = (size_t)c->n * c->q * sizeof(float);
-  const size_t per = host_chunk_bytes(c, chunk_frames, fbytes, ws_bytes(c->fft_plan, chunk_frames));
-  return host_chunks(c, prob_host, fbytes, frames, out_sym_host, out_iters_host, out_ok_host, chunk_frames,
-                     workspace_dev, workspace_bytes, per, cuda_stream,
-                     [&](const void* in, int nf, uint8_t* sy, int32_t* it, uint8_t* okb, void* ws, cudaStream_t s) {
-                       return fft_launch(c, reinterpret_cast<const float*>(in), nf, max_iters, early_stop, sy, it, okb,
-                                         nullptr, ws, s);
                      });
 }
 
