@@ -72,7 +72,8 @@ class CudaExecutor:
 class Server:
     """Native scheduler; device work by `executor` (a CudaExecutor, or a Python object with
     request_bytes(req), launch_bytes(reqs, plain), start(reqs, stream, plain) -> token,
-    done(token) -> bool and finish(token))."""
+    done(token) -> bool and finish(token)).  An exception raised by a Python executor is
+    re-raised by the submit or poll call that ran it; the server should then be discarded."""
 
     POLL_BATCH = 256
 
@@ -91,6 +92,7 @@ class Server:
         self._next_tag = 1
         self._tokens: dict[int, object] = {}   # Python executor tokens by native token
         self._next_token = 1
+        self._pending: BaseException | None = None   # raised by a Python executor inside a native call
         self._h = ctypes.c_void_p()
         L = binding.lib()
         plain = 1 if mode == "plain" else 0
@@ -107,53 +109,59 @@ class Server:
         self._buf = (ctypes.c_uint64 * self.POLL_BATCH)()
 
     # ---- Python executors behind the native scheduler
+    # An exception must not unwind through C: a callback records it and returns a
+    # neutral value (byte counts) or an error status (launch calls); the Python call
+    # that entered the native scheduler re-raises it (_raise_pending).
     def _make_callbacks(self):
         ex = self._ex
 
         def reqs_of(arr, n):
             return [self._tags[arr[i].contents.user] for i in range(n)]
 
+        def guarded(fn, failed):
+            def cb(*args):
+                try:
+                    return fn(*args)
+                except BaseException as e:  # noqa: BLE001 - re-raised after the native call
+                    if self._pending is None:
+                        self._pending = e
+                    return failed
+            return cb
+
         def request_bytes(_ctx, rp):
-            try:
-                return int(ex.request_bytes(self._tags[rp.contents.user]))
-            except Exception:  # noqa: BLE001 - a callback must not raise through C
-                return 0
+            return int(ex.request_bytes(self._tags[rp.contents.user]))
 
         def launch_bytes(_ctx, arr, n, plain):
-            try:
-                return int(ex.launch_bytes(reqs_of(arr, n), bool(plain)))
-            except Exception:  # noqa: BLE001
-                return 0
+            return int(ex.launch_bytes(reqs_of(arr, n), bool(plain)))
 
         def start(_ctx, arr, n, stream, plain, tok):
-            try:
-                reqs = reqs_of(arr, n)
-                now = self.clock()
-                for r in reqs:
-                    r.t_launch = now
-                k = self._next_token
-                self._next_token += 1
-                self._tokens[k] = ex.start(reqs, int(stream), bool(plain))
-                tok[0] = k
-                return binding.NBLDPC_OK
-            except Exception:  # noqa: BLE001
-                return binding.NBLDPC_ERR_ARG
+            reqs = reqs_of(arr, n)
+            now = self.clock()
+            for r in reqs:
+                r.t_launch = now
+            k = self._next_token
+            self._next_token += 1
+            self._tokens[k] = ex.start(reqs, int(stream), bool(plain))
+            tok[0] = k
+            return binding.NBLDPC_OK
 
         def done(_ctx, k):
-            try:
-                return 1 if ex.done(self._tokens[k]) else 0
-            except Exception:  # noqa: BLE001
-                return binding.NBLDPC_ERR_ARG
+            return 1 if ex.done(self._tokens[k]) else 0
 
         def finish(_ctx, k):
-            try:
-                ex.finish(self._tokens.pop(k))
-                return binding.NBLDPC_OK
-            except Exception:  # noqa: BLE001
-                return binding.NBLDPC_ERR_ARG
+            ex.finish(self._tokens.pop(k))
+            return binding.NBLDPC_OK
 
-        return (binding.REQUEST_BYTES_FN(request_bytes), binding.LAUNCH_BYTES_FN(launch_bytes),
-                binding.START_FN(start), binding.TOKEN_FN(done), binding.TOKEN_FN(finish))
+        err = binding.NBLDPC_ERR_ARG
+        return (binding.REQUEST_BYTES_FN(guarded(request_bytes, 0)),
+                binding.LAUNCH_BYTES_FN(guarded(launch_bytes, 0)),
+                binding.START_FN(guarded(start, err)), binding.TOKEN_FN(guarded(done, err)),
+                binding.TOKEN_FN(guarded(finish, err)))
+
+    def _raise_pending(self) -> None:
+        if self._pending is not None:
+            e, self._pending = self._pending, None
+            raise e
 
     # ---- arrivals
     def submit(self, req: Request, now: float | None = None) -> None:
@@ -179,8 +187,9 @@ class Server:
             r.out_ok_host = req.ok.data_ptr()
         self._tags[tag] = req
         rid = ctypes.c_uint64()
-        binding._check(binding.lib().nbldpc_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
-                       "nbldpc_server_submit")
+        st = binding.lib().nbldpc_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid))
+        self._raise_pending()
+        binding._check(st, "nbldpc_server_submit")
         self._ids[rid.value] = req
         req._tag = tag
 
@@ -190,8 +199,9 @@ class Server:
         L = binding.lib()
         n = ctypes.c_int()
         while True:
-            binding._check(L.nbldpc_server_poll(self._h, self._buf, self.POLL_BATCH, ctypes.byref(n)),
-                           "nbldpc_server_poll")
+            st = L.nbldpc_server_poll(self._h, self._buf, self.POLL_BATCH, ctypes.byref(n))
+            self._raise_pending()
+            binding._check(st, "nbldpc_server_poll")
             now = self.clock() if n.value else 0.0
             for i in range(n.value):
                 req = self._ids.pop(self._buf[i])

@@ -121,3 +121,31 @@ def test_plain_mode_serializes_single_requests():
 def test_percentile():
     xs = list(range(101))
     assert percentile(xs, 50) == 50 and percentile(xs, 99) == 99 and percentile(xs, 0) == 0
+
+
+def test_executor_errors_surface_in_python():
+    """An exception inside the Python executor is raised by the call that drove the scheduler."""
+    class Broken(FakeExecutor):
+        def start(self, reqs, stream, plain):
+            raise RuntimeError("device lost")
+
+    srv = Server(Broken(), budget_bytes=1 << 20, streams=1, clock=Clock())
+    srv.submit(req(0))
+    try:
+        srv.poll()
+    except RuntimeError as e:
+        assert "device lost" in str(e)
+    else:
+        raise AssertionError("the executor's exception was swallowed")
+
+    class BadBytes(FakeExecutor):
+        def request_bytes(self, r):
+            raise ValueError("no size")
+
+    srv2 = Server(BadBytes(), budget_bytes=1 << 20, streams=1, clock=Clock())
+    try:
+        srv2.submit(req(1))
+    except ValueError as e:
+        assert "no size" in str(e)
+    else:
+        raise AssertionError("the executor's exception was swallowed")
