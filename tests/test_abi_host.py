@@ -116,3 +116,22 @@ def test_server_arguments_are_checked(lib):
     st = lib.nbldpc_server_stats()
     assert L.nbldpc_server_stats_get(None, ctypes.byref(st)) == lib.NBLDPC_ERR_ARG
     L.nbldpc_server_destroy(None)
+
+
+def test_header_and_library_from_plain_c(lib, tmp_path):
+    """tests/c/abi_c99.c: the header compiles as C99 with warnings as errors, the program links
+    against the library and its argument checks pass (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    libdir = os.path.dirname(lib.LIB_PATH)
+    exe = str(tmp_path / "abi_c99")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                           os.path.join(here, "c", "abi_c99.c"), "-L", libdir, "-lnbldpc",
+                           f"-Wl,-rpath,{libdir}", "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert "c99 abi ok" in out.stdout
