@@ -199,10 +199,18 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def convolutions_per_frame_iter(code, table1=False):
+    """XOR min-max convolutions of one check-node pass: per check of degree d,
+    3(d-2) (forward and backward over d-2 edges, d-2 middle outputs) or, with
+    `table1`, the 3d-4 of Table 1 of the paper (forward and backward over d-1
+    edges each)."""
+    d = np.diff(code.row_ptr).astype(np.int64)
+    return int((3 * d - 4).sum()) if table1 else int((3 * np.maximum(d - 2, 0)).sum())
+
+
 def pairs_per_frame_iter(code):
     """Min-max pairs of one check-node pass: sum over checks of 3(d-2) q^2."""
-    d = np.diff(code.row_ptr).astype(np.int64)
-    return int((3 * np.maximum(d - 2, 0)).sum()) * code.q * code.q
+    return convolutions_per_frame_iter(code) * code.q * code.q
 
 
 def run_mixed(args, ws, rank, local):
@@ -491,11 +499,15 @@ FP32_LANES_PER_SM = 128
 
 
 def fft_flops_per_frame_iter(code):
-    """Float operations of one FFT-SPA iteration (Table 1 of the paper, FFT-SPA
-    rows without loop control): per check of degree d, two radix-2 transforms
-    of q log2 q additions per edge, d (d - 1) q products and d q scalings; per
-    variable of degree v, v (v - 1) q + v q products, v q additions for the
-    normalization sum and v q normalizing multiplications."""
+    """Float operations executed in one FFT-SPA iteration: per check of degree
+    d, two radix-2 transforms of q log2 q additions per edge, d (d - 1) q
+    products and d q scalings; per variable of degree v, v (v - 1) q + v q
+    products, v q additions for the normalization sum and v q normalizing
+    multiplications.  These are the FFT-SPA rows of Table 1 of the paper
+    without loop control, less two entries that execute no float operation
+    here: the transforms' multiplications (factors of +-1, folded into each
+    butterfly's add or subtract) and the additions listed beside the
+    check-node products."""
     d = np.diff(code.row_ptr).astype(np.int64)
     v = np.bincount(code.col_idx, minlength=code.n).astype(np.int64)
     q, lq = code.q, code.p
@@ -686,8 +698,7 @@ def run_schedule(args, ws, rank, local):
             torch.cuda.synchronize()
             t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
             its_h = its.cpu().numpy().astype(np.int64)
-            d = np.diff(code.row_ptr).astype(np.int64)
-            convs = int((3 * d - 4).sum()) if sched == binding.NBLDPC_CNP_TABLE1 else int((3 * (d - 2)).sum())
+            convs = convolutions_per_frame_iter(code, table1=sched == binding.NBLDPC_CNP_TABLE1)
             pairs = int(its_h.sum()) * convs * code.q * code.q
             res[label] = {"value": args.steps * frames * code.k * code.p / t / 1e6, "unit": "Mbit/s",
                           "ms_per_step": 1e3 * t / args.steps, "convolutions_per_check": convs // code.m,

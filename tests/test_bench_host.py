@@ -48,6 +48,89 @@ def test_irregular_counts_sum_over_rows_and_columns():
     assert bench.fft_flops_per_frame_iter(code) == want
 
 
+# ---- Table 1 of the paper (operation counts per iteration; memory transactions left out)
+# Each row restated as (additions, multiplications, divisions, comparisons) for a regular
+# code with M checks of degree dc, N variables of degree dv and field order g.
+
+def _table1_minmax(M, N, dc, dv, g):
+    lc_c = M + M * dc + M * dc * g          # loop control of the per-check passes
+    lc_v = N + N * dv + N * dv * g
+    return {
+        "fb_first_lc": (lc_c, 0, 0, lc_c),
+        "fb_first": (0, 0, 0, M * dc * g),
+        "fb_rest_lc": (M * (dc - 1) * g * g, 0, 0, M * (dc - 1) * g * g),
+        "fb_rest": (2 * M * (dc - 1) * g * g, 0, 0, 2 * M * (dc - 1) * g * g + 2 * M * (dc - 1) * g),
+        "beta_ends_lc": (lc_c, 0, 0, lc_c),
+        "beta_ends": (0, 0, 0, 2 * M * dc * g),
+        "beta_rest_lc": (M * (dc - 2) * g * g, 0, 0, M * (dc - 2) * g * g),
+        "beta_rest": (M * (dc - 2) * g * g, 0, 0, M * (dc - 2) * g * g + M * (dc - 2) * g),
+        "vnp_lc": (lc_v, 0, 0, lc_v),
+        "vnp": (N * dv * (dv - 1) * g + 2 * N * dv * g, 0, 0, N * dv * g),
+    }
+
+
+def _table1_fftspa(M, N, dc, dv, g, lg):
+    lc_c = M + M * dc + M * dc * g
+    lc_v = N + N * dv + N * dv * g
+    e = M * dc
+    return {
+        "perm_lc": (lc_v, 0, 0, lc_v),
+        "perm": (0, 0, 0, 0),
+        "cnp_lc": (lc_c, 0, 0, lc_c),
+        "fft": (e * g * lg, e * g * lg, 0, 0),
+        "product": (e * (dc - 1) * g, e * (dc - 1) * g, 0, 0),
+        "ifft": (e * g * lg, e * g * lg, e * g, 0),
+        "deperm_lc": (lc_c, 0, 0, lc_c),
+        "deperm": (0, 0, 0, 0),
+        "vnp_lc": (lc_v, 0, 0, lc_v),
+        "vnp": (N * dv * g, N * dv * (dv - 1) * g + N * dv * g, N * dv * g, 0),
+    }
+
+
+SHAPES = [(24, 48, 4, 2, 4, 2), (288, 576, 4, 2, 64, 6), (300, 600, 6, 3, 32, 5), (32, 128, 8, 2, 256, 8),
+          (7, 21, 9, 3, 8, 3)]
+
+
+@pytest.mark.parametrize("M,N,dc,dv,g,lg", SHAPES)
+def test_table1_rows_sum_to_the_printed_totals(M, N, dc, dv, g, lg):
+    """Sec. 3's closed forms for the total operation counts (memory transactions excluded) are
+    the sums of Table 1's rows, for both decoders."""
+    mm = sum(sum(r) for r in _table1_minmax(M, N, dc, dv, g).values())
+    assert mm == (4 * M + 4 * M * dc - 4 * M * g - 14 * M * g * g + 10 * M * dc * g + 10 * M * dc * g * g
+                  + 2 * N + 2 * N * dv + 4 * N * dv * g + N * dv * dv * g)
+    ff = sum(sum(r) for r in _table1_fftspa(M, N, dc, dv, g, lg).values())
+    assert ff == (4 * M + 4 * M * dc + 3 * M * dc * g + 2 * M * dc * dc * g + 4 * M * dc * g * lg
+                  + 4 * N + 4 * N * dv + 6 * N * dv * g + N * dv * dv * g)
+
+
+@pytest.mark.parametrize("name", ["gf4_n48_dv2_dc4", "gf64_n576_dv2_dc4", "gf32_n600_dv3_dc6",
+                                  "gf256_n128_dv2_dc8"])
+def test_convolution_counts_against_table1(name):
+    """Table 1 lists one GF addition (the XOR of the two indices) per min-max pair of the
+    forward/backward and middle convolutions: M(3dc - 4) g^2 pairs, the count of the Table 1
+    schedule; the minimal schedule drops the two convolutions whose outputs no message uses."""
+    code = I.workload_code(name)
+    w = I.WORKLOADS[name]
+    rows = _table1_minmax(code.m, code.n, w["dc"], w["dv"], code.q)
+    t1_pairs = rows["fb_rest"][0] + rows["beta_rest"][0]
+    assert bench.convolutions_per_frame_iter(code, table1=True) * code.q ** 2 == t1_pairs
+    assert bench.convolutions_per_frame_iter(code) * code.q ** 2 == t1_pairs - 2 * code.m * code.q ** 2
+    assert bench.pairs_per_frame_iter(code) == t1_pairs - 2 * code.m * code.q ** 2
+
+
+@pytest.mark.parametrize("name", ["gf4_n48_dv2_dc4", "gf64_n576_dv2_dc4", "gf32_n600_dv3_dc6",
+                                  "gf256_n128_dv2_dc8"])
+def test_fftspa_count_against_table1(name):
+    """The float-operation count is Table 1's FFT-SPA rows without loop control, less the
+    transforms' multiplications (+-1 factors) and the additions beside the check-node products."""
+    code = I.workload_code(name)
+    w = I.WORKLOADS[name]
+    rows = _table1_fftspa(code.m, code.n, w["dc"], w["dv"], code.q, code.p)
+    no_lc = sum(sum(r) for k, r in rows.items() if not k.endswith("_lc"))
+    dropped = rows["fft"][1] + rows["ifft"][1] + rows["product"][0]
+    assert bench.fft_flops_per_frame_iter(code) == no_lc - dropped
+
+
 def test_command_line_lists_every_workload():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True,
                          text=True, check=True).stdout
