@@ -28,6 +28,8 @@
 // log2(R) + 1 table reads per edge give all R gather (and scatter) indices.
 #pragma once
 
+#include <type_traits>
+
 #include "mma_kernels.cuh"   // CodeBlob, ilog2, group_mask
 
 namespace nbldpc {
@@ -177,6 +179,168 @@ __device__ __forceinline__ void wht_inv(float (&v)[g::R], int gl, unsigned gmask
     if constexpr (HalfExchange<g>::v) lane_stage<g>(v, k, gl, gmask);
     else lane_stage_full<g>(v, k, gl, gmask);
   }
+}
+
+// ---- select-free butterflies (half exchanges for 8 <= q <= 64, R = 4)
+// Every butterfly is computed as
+//     out_lo = recv + x * keep,   out_hi = recv - x * keep        (one FMA each)
+// into registers (r, r | c), with x = +-1 a per-lane constant of the stage.
+// In a lane stage both lanes of a pair keep register r and send register
+// r | c: the upper lane holds its elements with register bit c relabelled, so
+// the half exchange needs no selects.  A stored value is then a sign times
+// the transform element at some index; which output gets the sum (the sign
+// of x) is chosen per lane so that each stage leaves the relabelling the next
+// stage on the same register bit needs, and the signs follow.  Layout and
+// signs depend on the field order only, so a compile-time run of the stages
+// (make_fft_signs) gives the lanes whose coefficient is -1 at every stage
+// and the signs of the inverse outputs (folded into the final 1/q scale).
+// The inverse starts from the forward signs raised to the number of factors of
+// the product, odd here (check-degree buckets 4 and 8), i.e. the forward
+// signs themselves; its outputs are back in natural order (element
+// lane * R + r in register r).
+struct FftSigns {
+  uint32_t fwd[8];   // forward stage s (RB register stages, then lane stages 0..K-1): bit gl = coefficient -1
+  uint32_t inv[8];   // inverse stage s (RB register stages, then lane stages K-1..0)
+  uint32_t out[8];   // register r: bit gl = the inverse output in register r of lane gl is the negated element
+  bool ok;           // every stage paired single-bit index pairs, coefficients independent of r, natural order out
+};
+
+// One butterfly on (keep, recv) = (sign, index) pairs with the sum placed in
+// out_lo when eps = +1, in out_hi when eps = -1; returns x = eps * s_recv * s_keep.
+__host__ __device__ constexpr int sf_bfly(int ik, int sk, int ir, int sr, int eps, int& ilo, int& slo, int& ihi,
+                                          int& shi, bool& ok) {
+  const int t = ik ^ ir;
+  if (t == 0 || (t & (t - 1)) != 0) ok = false;
+  const int lo = ik < ir ? ik : ir, hi = lo | t;
+  // recv + e * x * keep carries sign s_recv; it is the sum for e = eps, the
+  // difference (index hi) for e = -eps, negated when recv is the upper element
+  const bool recv_lo = ir == lo;
+  ilo = lo; slo = sr;                                 // e = eps: the sum
+  ihi = hi; shi = recv_lo ? sr : -sr;                 // e = -eps: the difference
+  if (eps < 0) {                                      // sum into out_hi
+    const int ti = ilo, ts = slo;
+    ilo = ihi; slo = shi; ihi = ti; shi = ts;
+  }
+  return eps * sr * sk;
+}
+
+template <int Q, int R> __host__ __device__ constexpr FftSigns make_fft_signs() {
+  constexpr int G = Q / R;
+  int RB = 0, LQ = 0;
+  while ((1 << RB) < R) ++RB;
+  while ((1 << LQ) < Q) ++LQ;
+  const int K = LQ - RB;
+  FftSigns T{};
+  T.ok = G >= 2 && K >= 1 && RB + K <= 8;
+  int idx[Q] = {}, sg[Q] = {}, ni[Q] = {}, ns[Q] = {};
+  int m0[G] = {};           // initial relabelling: bit c_k of lane gl is bit k of gl, k < RB
+  for (int gl = 0; gl < G; ++gl)
+    for (int k = 0; k < K && k < RB; ++k) m0[gl] |= ((gl >> k) & 1) << (k % RB);
+  for (int gl = 0; gl < G; ++gl)
+    for (int p = 0; p < R; ++p) { idx[gl * R + p] = (gl << RB) | (p ^ m0[gl]); sg[gl * R + p] = 1; }
+  // one stage: register stage (lane_stage false, bit b) or lane stage (bit k);
+  // the eps rule picks, per lane, where the sum goes
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int st = 0; st < RB + K; ++st) {
+      const bool lane_st = st >= RB;
+      const int b = st;                                         // register stage bit
+      const int k = !lane_st ? 0 : (pass == 0 ? st - RB : K - 1 - (st - RB));   // lane stage lane bit
+      const int c = lane_st ? 1 << (k % RB) : 1 << b;
+      uint32_t& mask = pass == 0 ? T.fwd[st] : T.inv[st];
+      for (int i = 0; i < Q; ++i) { ni[i] = idx[i]; ns[i] = sg[i]; }
+      for (int gl = 0; gl < G; ++gl) {
+        int xl = 0;
+        for (int r = 0; r < R; ++r) {
+          if (r & c) continue;
+          const int kp = gl * R + r;
+          const int rp = lane_st ? (gl ^ (1 << k)) * R + (r | c) : gl * R + (r | c);
+          int eps = 1;
+          if (!lane_st) {
+            // keep the relabelling: the sum goes to the slot of the lower index
+            eps = idx[kp] < idx[rp] ? 1 : -1;
+          } else if (pass == 0) {
+            // relabel register bit c for its next use: lane stage k + RB, else the inverse's stage k
+            const int nxt = k + RB < K ? k + RB : k;
+            eps = ((gl >> nxt) & 1) ? -1 : 1;
+          } else {
+            // inverse: relabel for lane stage k - RB, natural order after the last use
+            eps = (k - RB >= 0 && ((gl >> (k - RB)) & 1)) ? -1 : 1;
+          }
+          int ilo = 0, slo = 0, ihi = 0, shi = 0;
+          const int x = sf_bfly(idx[kp], sg[kp], idx[rp], sg[rp], eps, ilo, slo, ihi, shi, T.ok);
+          if (xl == 0) xl = x;
+          else if (xl != x) T.ok = false;
+          ni[kp] = ilo; ns[kp] = slo;
+          ni[gl * R + (r | c)] = ihi; ns[gl * R + (r | c)] = shi;
+        }
+        if (xl < 0) mask |= 1u << gl;
+      }
+      for (int i = 0; i < Q; ++i) { idx[i] = ni[i]; sg[i] = ns[i]; }
+    }
+  }
+  for (int i = 0; i < Q; ++i) {
+    if (idx[i] != i) T.ok = false;
+    if (sg[i] < 0) T.out[i % R] |= 1u << (i / R);
+  }
+  return T;
+}
+
+#ifndef NBLDPC_FFT_SELECT_FREE
+#define NBLDPC_FFT_SELECT_FREE 1
+#endif
+template <class g> struct SelectFree {
+  static constexpr bool v = NBLDPC_FFT_SELECT_FREE && g::R == 4 && g::Q >= 8 && g::Q <= 64 && HalfExchange<g>::v;
+  static constexpr FftSigns T = make_fft_signs<(v ? g::Q : 8), 4>();
+  static_assert(!v || T.ok, "select-free butterfly schedule");
+};
+
+template <int I, int N, class F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// +-1 for this lane from a mask of lanes (bit gl set: -1), a constant when
+// every lane agrees.  A mask and its complement give the same value up to a
+// sign (a free operand negation), so the value is formed from the member of
+// the pair with lane 0 clear and equal classes share one register.
+template <uint32_t MASK, int G> __device__ __forceinline__ float sf_coef(int gl) {
+  constexpr uint32_t all = G >= 32 ? 0xFFFFFFFFu : (1u << G) - 1;
+  constexpr uint32_t m = MASK & all, base = (m & 1u) ? (m ^ all) : m;
+  constexpr float sign = (m & 1u) ? -1.f : 1.f;
+  if constexpr (base == 0) return sign;
+  else return sign * (((base >> gl) & 1) ? -1.f : 1.f);
+}
+
+template <class g, bool INV>
+__device__ __forceinline__ void wht_sf(float (&v)[g::R], int gl, unsigned gmask) {
+  constexpr FftSigns T = SelectFree<g>::T;
+  constexpr int RB = g::RB, K = g::LQ - g::RB;
+  static_for<0, RB>([&](auto S) {
+    constexpr int b = decltype(S)::value, h = 1 << b;
+    const float x = sf_coef<INV ? T.inv[b] : T.fwd[b], g::G>(gl);
+#pragma unroll
+    for (int r = 0; r < g::R; ++r) {
+      if (r & h) continue;
+      const float keep = v[r], recv = v[r | h];
+      v[r] = fmaf(x, keep, recv);
+      v[r | h] = fmaf(-x, keep, recv);
+    }
+  });
+  static_for<0, K>([&](auto S) {
+    constexpr int s = decltype(S)::value;
+    constexpr int k = INV ? K - 1 - s : s, c = 1 << (k % RB);
+    const float x = sf_coef<INV ? T.inv[RB + s] : T.fwd[RB + s], g::G>(gl);
+#pragma unroll
+    for (int r = 0; r < g::R; ++r) {
+      if (r & c) continue;
+      const float keep = v[r];
+      const float recv = __shfl_xor_sync(gmask, v[r | c], 1 << k);
+      v[r] = fmaf(x, keep, recv);
+      v[r | c] = fmaf(-x, keep, recv);
+    }
+  });
 }
 
 // idx[r] = h^-1 (y0 ^ r) for the lane's elements y0 ^ r (y0 = lane * R), from
@@ -482,23 +646,46 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
   // depermutation), one group of G lanes per check
   auto cnp = [&](bool first) {
     if constexpr (DC > 0) {
+    constexpr bool SF = SelectFree<g>::v;
+    constexpr FftSigns T = SelectFree<g>::T;
+    static_assert(!SF || DC % 2 == 0, "the select-free inverse expects an odd number of product factors");
+    // select-free form: the lane gathers its elements with the initial relabelling
+    // (register bit k carries lane bit k, k < RB) and scales its outputs by +-1/q
+    constexpr int RL = (g::LQ - g::RB) < g::RB ? (g::LQ - g::RB) : g::RB;
+    const int y0s = SF ? (y0 ^ (gl & ((1 << RL) - 1))) : y0;
+    const bool y0snz = y0s != 0;
+    const int ly0s = y0snz ? glog[y0s] : 0;
     for (int r = grp; r < job.m; r += ngroups) {
       const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
       float W[DC][R];
+      // absent edges (d < DC) enter the product as the transform of the unit
+      // vector at 0, all ones; in the select-free form an odd number of them
+      // must carry the forward output signs (one such factor, the others 1)
+      float pad[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) pad[i] = 1.f;
+      if constexpr (SF) {
+        if (d < DC && ((DC - d) & 1)) {
+#pragma unroll
+          for (int i = 0; i < R; ++i) pad[i] = (y0s == 0 && i == 0) ? 1.f : 0.f;
+          wht_sf<g, false>(pad, gl, gmask);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < DC; ++j) {
         if (j < d) {
           const int e = e0 + j;
           int idx[R];
-          perm_index<g>(idx, exp2, edge_lhi[e], ly0, y0nz);
+          perm_index<g>(idx, exp2, edge_lhi[e], ly0s, y0snz);
           // u'_j(y) = u_j(h_j^-1 y); u^(0) = p on the first pass
           const float* src = first ? pf + (size_t)edge_col[e] * Q : X + (size_t)e * Q;
 #pragma unroll
           for (int i = 0; i < R; ++i) W[j][i] = src[idx[i]];
-          wht_fwd<g>(W[j], gl, gmask);
+          if constexpr (SF) wht_sf<g, false>(W[j], gl, gmask);
+          else wht_fwd<g>(W[j], gl, gmask);
         } else {
 #pragma unroll
-          for (int i = 0; i < R; ++i) W[j][i] = 1.f;   // transform of the unit vector at 0
+          for (int i = 0; i < R; ++i) W[j][i] = j == d ? pad[i] : 1.f;
         }
       }
 #pragma unroll
@@ -513,14 +700,18 @@ __device__ __forceinline__ void fft_decode_frame(const FftJob& job, int frame, f
               if (k != j) t *= W[k][i];
             v[i] = t;
           }
-          wht_inv<g>(v, gl, gmask);
+          if constexpr (SF) wht_sf<g, true>(v, gl, gmask);
+          else wht_inv<g>(v, gl, gmask);
           const int e = e0 + j;
           int idx[R];
           perm_index<g>(idx, exp2, edge_lhi[e], ly0, y0nz);
           // v'_j(h_j^-1 y) = v_j(y): inverse transform / q, negative rounding -> 0
           float* dst = X + (size_t)e * Q;
-#pragma unroll
-          for (int i = 0; i < R; ++i) dst[idx[i]] = fmaxf(v[i] * (1.f / Q), 0.f);
+          static_for<0, R>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const float t = SF ? v[i] * sf_coef<T.out[i], g::G>(gl) : v[i];
+            dst[idx[i]] = fmaxf(t * (1.f / Q), 0.f);
+          });
         }
       }
     }
