@@ -80,22 +80,48 @@ def dist_setup(args):
     return ws, rank, local
 
 
-def kernel_source_hash(source: str = "mma_kernels.cuh") -> str:
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", source), "rb") as fh:
-        h.update(fh.read())
-    return h.hexdigest()[:16]
+def strip_comments(text: str) -> str:
+    """C/C++ source without comments, whitespace runs collapsed to one space (string and
+    character literals kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def kernel_code_hash(source: str = "mma_kernels.cuh") -> str:
+    """Fingerprint of a kernel header's code: sha256 of the source without comments and
+    with whitespace collapsed, so that a comment edit keeps its profile."""
+    with open(os.path.join(ROOT, "paper_2508_03567_gb300", "csrc", source), encoding="utf-8") as fh:
+        code = strip_comments(fh.read())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(profile: str = "mma_decode_kernel_gf64_n576.md", source: str = "mma_kernels.cuh"):
-    """DRAM bytes per frame from a committed ncu summary, if it was taken on the current kernel source."""
+    """DRAM bytes per frame from a committed ncu summary, if it was taken on the current kernel code."""
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None, None
     txt = open(path).read()
-    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_hash = re.search(r"kernel_code_sha256_16:\s*([0-9a-f]+)", txt)
     m_bpf = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", txt)
-    if not m_hash or not m_bpf or m_hash.group(1) != kernel_source_hash(source):
+    if not m_hash or not m_bpf or m_hash.group(1) != kernel_code_hash(source):
         return None, path
     return float(m_bpf.group(1)), path
 

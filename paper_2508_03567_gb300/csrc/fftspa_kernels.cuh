@@ -17,8 +17,8 @@
 // two forms.  Distributed (q >= 8, check degree <= 8): a check vector is
 // spread over G lanes of R elements each (element y = lane * R + r);
 // butterflies on the bits of r run in registers, those on the lane bits
-// through half exchanges between partner lanes (q <= 64: one shuffle per two
-// butterfly inputs) or one shuffle per element (q >= 128).  Lane per edge
+// through select-free half exchanges between partner lanes (one shuffle per
+// two butterfly inputs, one FMA per output; see wht_sf).  Lane per edge
 // (q <= 4, or a check of degree 9..32): one lane holds a whole vector and the
 // permutation moves into the transform domain (see cnp_lane).
 //
@@ -57,10 +57,11 @@ struct FftParams {
 };
 
 // Elements per lane and block size of the distributed check-node form at
-// q = 64 and q = 128, and the largest q with half-exchange lane stages
-// (compile-time tuning knobs; the defaults are the measured best on GB300:
-// GF(64) (2,4) N=576: 4 elements / 768 threads 1.19 Gbit/s, 8 / 768 0.97,
-// 16 / 512 0.72, 2 / 1024 1.05, 4 / 896 1.08; GF(128) (2,4) N=256: 4
+// q = 64 and q = 128, and the largest q with select-based half-exchange lane
+// stages where the select-free form is switched off (compile-time tuning
+// knobs; the defaults are the measured best on GB300, with select-based lane
+// stages: GF(64) (2,4) N=576: 4 elements / 768 threads 1.19 Gbit/s, 8 / 768
+// 0.97, 16 / 512 0.72, 2 / 1024 1.05, 4 / 896 1.08; GF(128) (2,4) N=256: 4
 // elements 0.81, 8 elements 0.71).
 #ifndef NBLDPC_FFT_R64
 #define NBLDPC_FFT_R64 4
@@ -112,6 +113,10 @@ __device__ __forceinline__ void wht_regs(float (&v)[g::R]) {
   }
 }
 
+// Select-based lane stages (lane_stage, lane_stage_full, wht_fwd, wht_inv):
+// the forms for field orders above NBLDPC_FFT_SELECT_FREE_MAXQ, a tuning knob
+// that by default gives every field the select-free form.
+//
 // Butterfly over lane bit k by half exchanges: the lanes of a pair (gl, gl ^ 2^k)
 // hold the same register indices of the two elements of each butterfly; the
 // lower lane keeps registers with bit c = 2^(k mod RB) clear and sends the
@@ -141,9 +146,11 @@ __device__ __forceinline__ void lane_stage(float (&v)[g::R], int k, int gl, unsi
 
 // Butterfly over lane bit k with every element shuffled: the upper lane of
 // the pair computes partner - own, the lower own + partner (layout unchanged).
-// Used for q >= 128, where the selects of the half exchange cost more than
-// the shuffles they save (measured on GB300: GF(256) -8 % with half
-// exchanges; GF(16) +7 %, GF(8) / GF(64) +1 %, GF(32) -1 %).
+// Taken above NBLDPC_FFT_HALF_MAXQ: at q >= 128 the selects of the
+// select-based half exchange cost more than the shuffles they save (measured
+// on GB300: GF(256) -8 % with half exchanges; GF(16) +7 %, GF(8) / GF(64)
+// +1 %, GF(32) -1 %).  The select-free form beats both (GF(128) 811 -> 887
+// Mbit/s, GF(256) 550 -> 556 against this one).
 template <class g>
 __device__ __forceinline__ void lane_stage_full(float (&v)[g::R], int k, int gl, unsigned gmask) {
   const int o = 1 << k;
@@ -181,7 +188,7 @@ __device__ __forceinline__ void wht_inv(float (&v)[g::R], int gl, unsigned gmask
   }
 }
 
-// ---- select-free butterflies (half exchanges for 8 <= q <= 64, R = 4)
+// ---- select-free butterflies (half exchanges for q >= 8, R = 4 or 8)
 // Every butterfly is computed as
 //     out_lo = recv + x * keep,   out_hi = recv - x * keep        (one FMA each)
 // into registers (r, r | c), with x = +-1 a per-lane constant of the stage.
@@ -285,12 +292,15 @@ template <int Q, int R> __host__ __device__ constexpr FftSigns make_fft_signs() 
   return T;
 }
 
-#ifndef NBLDPC_FFT_SELECT_FREE
-#define NBLDPC_FFT_SELECT_FREE 1
+// Largest field order with select-free butterflies (compile-time knob; above
+// it, q <= NBLDPC_FFT_HALF_MAXQ takes the select-based half exchange and larger
+// fields one shuffle per element).
+#ifndef NBLDPC_FFT_SELECT_FREE_MAXQ
+#define NBLDPC_FFT_SELECT_FREE_MAXQ 256
 #endif
 template <class g> struct SelectFree {
-  static constexpr bool v = NBLDPC_FFT_SELECT_FREE && g::R == 4 && g::Q >= 8 && g::Q <= 64 && HalfExchange<g>::v;
-  static constexpr FftSigns T = make_fft_signs<(v ? g::Q : 8), 4>();
+  static constexpr bool v = (g::R == 4 || g::R == 8) && g::Q >= 8 && g::Q <= NBLDPC_FFT_SELECT_FREE_MAXQ;
+  static constexpr FftSigns T = make_fft_signs<(v ? g::Q : 8), (v ? g::R : 4)>();
   static_assert(!v || T.ok, "select-free butterfly schedule");
 };
 

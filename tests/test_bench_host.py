@@ -131,6 +131,18 @@ def test_fftspa_count_against_table1(name):
     assert bench.fft_flops_per_frame_iter(code) == no_lc - dropped
 
 
+def test_code_hash_ignores_comments_and_layout_only():
+    """The profile fingerprint: comments and whitespace do not count, code and literals do."""
+    a = "int f(int x) {  // twice\n  return 2 * x; /* doubled */ }\n"
+    b = "/* header */\nint f(int x) {\n\n  return 2 * x;\n}"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.strip_comments(a) == bench.strip_comments(b) == "int f(int x) { return 2 * x; }"
+    assert bench.strip_comments(c) != bench.strip_comments(a)
+    assert bench.strip_comments('s = "a // b /* c */";') == 's = "a // b /* c */";'
+    assert bench.strip_comments("char q = '\\''; // x") == "char q = '\\'';"
+    assert len(bench.kernel_code_hash("fftspa_kernels.cuh")) == 16
+
+
 def test_command_line_lists_every_workload():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True,
                          text=True, check=True).stdout

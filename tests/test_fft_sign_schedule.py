@@ -16,8 +16,8 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-POLY = {8: 0b1011, 16: 0b10011, 32: 0b100101, 64: 0b1000011}
-R, RB = 4, 2
+POLY = {8: 0b1011, 16: 0b10011, 32: 0b100101, 64: 0b1000011, 128: 0b10000011, 256: 0b100011101}
+LANE_ELEMS = {8: 4, 16: 4, 32: 4, 64: 4, 128: 4, 256: 8}     # elements per lane of the kernels
 
 
 @pytest.fixture(scope="module")
@@ -32,9 +32,10 @@ def tables(tmp_path_factory):
     tabs = {}
     for line in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines():
         t = line.split()
-        q = int(t[1])
+        q, r = int(t[1]), int(t[3])
+        assert r == LANE_ELEMS[q]
         i_f, i_i, i_o = t.index("fwd"), t.index("inv"), t.index("out")
-        tabs[q] = dict(ok=int(t[3]), fwd=[int(x, 16) for x in t[i_f + 1:i_i]],
+        tabs[q] = dict(ok=int(t[5]), fwd=[int(x, 16) for x in t[i_f + 1:i_i]],
                        inv=[int(x, 16) for x in t[i_i + 1:i_o]], out=[int(x, 16) for x in t[i_o + 1:]])
     return tabs
 
@@ -61,6 +62,8 @@ def coef(mask, gl):
 
 def wht_sf(V, q, masks):
     """The kernel's select-free stages: RB register stages, then the lane stages."""
+    R = LANE_ELEMS[q]
+    RB = R.bit_length() - 1
     G, K = q // R, q.bit_length() - 1 - RB
     inv_order = masks is not None and masks[1]
     masks = masks[0]
@@ -88,6 +91,8 @@ def wht_sf(V, q, masks):
 
 def kernel_model(q, DC, us, hs, T):
     mul, inv = field(q)
+    R = LANE_ELEMS[q]
+    RB = R.bit_length() - 1
     G, K = q // R, q.bit_length() - 1 - RB
     d = len(us)
     y0 = np.arange(G) * R
@@ -133,25 +138,23 @@ def brute_force(q, us, hs):
             if k == j:
                 continue
             nxt = np.zeros(q)
-            for s in range(q):
-                if acc[s]:
-                    for c in range(q):
-                        nxt[s ^ mul(hs[k], c)] += acc[s] * us[k][c]
+            for c in range(q):              # every running sum s moves to s + h_k c
+                nxt[np.arange(q) ^ mul(hs[k], c)] += acc * us[k][c]
             acc = nxt
         outs.append(np.array([acc[mul(hs[j], x)] for x in range(q)]))
     return outs
 
 
 def test_tables_are_consistent(tables):
-    assert sorted(tables) == [8, 16, 32, 64]
+    assert sorted(tables) == [8, 16, 32, 64, 128, 256]
     for q, T in tables.items():
         assert T["ok"] == 1, q
         assert len(T["fwd"]) == len(T["inv"]) == q.bit_length() - 1
-        G = q // R
+        G = q // LANE_ELEMS[q]
         assert all(m < (1 << G) for m in T["fwd"] + T["inv"] + T["out"]), q
 
 
-@pytest.mark.parametrize("q", [8, 16, 32, 64])
+@pytest.mark.parametrize("q", [8, 16, 32, 64, 128, 256])
 @pytest.mark.parametrize("DC,degrees", [(4, (2, 3, 4)), (8, (2, 5, 6, 8))])
 def test_model_matches_brute_force(tables, q, DC, degrees):
     rng = np.random.default_rng(q * 10 + DC)
@@ -169,7 +172,7 @@ def test_a_wrong_coefficient_is_caught(tables):
     """Flipping one lane's coefficient in one stage breaks the check update."""
     q, DC = 16, 4
     T = {k: (list(v) if isinstance(v, list) else v) for k, v in tables[q].items()}
-    T["fwd"][RB] ^= 1 << 1
+    T["fwd"][2] ^= 1 << 1
     rng = np.random.default_rng(3)
     us = [rng.random(q) for _ in range(4)]
     hs = [3, 5, 7, 9]
