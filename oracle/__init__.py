@@ -49,6 +49,8 @@ def lib():
             L.orc_gf_tables.argtypes = [ctypes.c_int, ctypes.c_uint, i32p, i32p]
             L.orc_gf_mul_all.argtypes = [ctypes.c_int, ctypes.c_uint, i32p, i32p]
             L.orc_check_update.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, i32p, u8p, u8p]
+            L.orc_check_update_counted.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, i32p, u8p, u8p,
+                                                   ctypes.POINTER(ctypes.c_longlong)]
             L.orc_decode.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                      i32p, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, u8p, i32p, u8p]
@@ -101,6 +103,21 @@ def check_update(q: int, poly: int, h, alpha: np.ndarray) -> np.ndarray:
     if rc:
         raise ValueError("invalid check")
     return b
+
+
+def check_update_pairs(q: int, poly: int, h, alpha: np.ndarray):
+    """(beta [d, q], pairs [3]): the check update and the (x', x'') pairs its forward, backward
+    and beta remaining-edge blocks visited."""
+    h = np.ascontiguousarray(h, np.int32)
+    a = np.ascontiguousarray(alpha, np.uint8)
+    d = h.size
+    b = np.zeros((d, q), np.uint8)
+    pairs = np.zeros(3, np.int64)
+    rc = lib().orc_check_update_counted(q, poly, d, _p(h, ctypes.c_int32), _p(a, ctypes.c_uint8),
+                                        _p(b, ctypes.c_uint8), _p(pairs, ctypes.c_longlong))
+    if rc:
+        raise ValueError("invalid check")
+    return b, pairs
 
 
 def _code_arrays(code):

@@ -64,8 +64,11 @@ int orc_gf_mul_all(int q, unsigned poly, int32_t *mul_out /* q*q */, int32_t *in
  * the one output symbol it constrains.                                      */
 #define BIG 0x7fffffff
 
+/* pairs (optional, [3]): pairs (x', x'') visited by the F, B and beta
+ * "remaining edges" blocks, counted row by row as they run (the work that
+ * Table 1 tabulates per block). */
 static void cnp_one_check(const gf_t *g, int d, const int *h, int *const *alpha, int *const *beta,
-                          int *F /* d*q */, int *B /* d*q */) {
+                          int *F /* d*q */, int *B /* d*q */, long long *pairs) {
   const int q = g->q;
   /* F & B: first edges */
   const int hinv_first = gf_inv(g, h[0]), hinv_last = gf_inv(g, h[d - 1]);
@@ -76,22 +79,26 @@ static void cnp_one_check(const gf_t *g, int d, const int *h, int *const *alpha,
   /* F: remaining edges, n = 1..d-2 (F_{d-1} is never used) */
   for (int n = 1; n <= d - 2; n++) {
     for (int x = 0; x < q; x++) F[n * q + x] = BIG;
-    for (int x1 = 0; x1 < q; x1++)          /* x'  */
+    for (int x1 = 0; x1 < q; x1++) {        /* x'  */
+      if (pairs) pairs[0] += q;
       for (int x2 = 0; x2 < q; x2++) {      /* x'' */
         int x = x1 ^ gf_mul(g, h[n], x2);
         int v = F[(n - 1) * q + x1] > alpha[n][x2] ? F[(n - 1) * q + x1] : alpha[n][x2];
         if (v < F[n * q + x]) F[n * q + x] = v;
       }
+    }
   }
   /* B: remaining edges, B_{n-1} from B_n for n = d-1 down to 2 (B_0 unused) */
   for (int n = d - 1; n >= 2; n--) {
     for (int x = 0; x < q; x++) B[(n - 1) * q + x] = BIG;
-    for (int x1 = 0; x1 < q; x1++)
+    for (int x1 = 0; x1 < q; x1++) {
+      if (pairs) pairs[1] += q;
       for (int x2 = 0; x2 < q; x2++) {
         int x = x1 ^ gf_mul(g, h[n - 1], x2);
         int v = B[n * q + x1] > alpha[n - 1][x2] ? B[n * q + x1] : alpha[n - 1][x2];
         if (v < B[(n - 1) * q + x]) B[(n - 1) * q + x] = v;
       }
+    }
   }
   /* beta: first and last edge */
   for (int x = 0; x < q; x++) {
@@ -102,19 +109,22 @@ static void cnp_one_check(const gf_t *g, int d, const int *h, int *const *alpha,
   for (int n = 1; n <= d - 2; n++) {
     const int hinv = gf_inv(g, h[n]);
     for (int x = 0; x < q; x++) beta[n][x] = BIG;
-    for (int x1 = 0; x1 < q; x1++)          /* x'  */
+    for (int x1 = 0; x1 < q; x1++) {        /* x'  */
+      if (pairs) pairs[2] += q;
       for (int x3 = 0; x3 < q; x3++) {      /* x'' */
         /* x' + h_n x = x''  <=>  x = h_n^-1 (x' + x'') */
         int x = gf_mul(g, hinv, x1 ^ x3);
         int v = F[(n - 1) * q + x3] > B[(n + 1) * q + x1] ? F[(n - 1) * q + x3] : B[(n + 1) * q + x1];
         if (v < beta[n][x]) beta[n][x] = v;
       }
+    }
   }
 }
 
-/* Exported single-check update (for the brute-force pin). */
-int orc_check_update(int q, unsigned poly, int d, const int32_t *h, const uint8_t *alpha_in /* d*q */,
-                     uint8_t *beta_out /* d*q */) {
+/* Exported single-check update (for the brute-force pin); pairs (optional,
+ * [3]) receives the pairs visited by the F, B and beta remaining-edge blocks. */
+int orc_check_update_counted(int q, unsigned poly, int d, const int32_t *h, const uint8_t *alpha_in /* d*q */,
+                             uint8_t *beta_out /* d*q */, long long *pairs) {
   gf_t g;
   if (gf_build(&g, q, poly) || d < 2) return -1;
   for (int j = 0; j < d; j++)
@@ -129,10 +139,16 @@ int orc_check_update(int q, unsigned poly, int d, const int32_t *h, const uint8_
     bp[j] = b + j * q;
     for (int x = 0; x < q; x++) a[j * q + x] = alpha_in[j * q + x];
   }
-  cnp_one_check(&g, d, hh, ap, bp, F, B);
+  if (pairs) pairs[0] = pairs[1] = pairs[2] = 0;
+  cnp_one_check(&g, d, hh, ap, bp, F, B, pairs);
   for (int i = 0; i < d * q; i++) beta_out[i] = (uint8_t)b[i];
   free(a); free(b); free(F); free(B); free(ap); free(bp);
   return 0;
+}
+
+int orc_check_update(int q, unsigned poly, int d, const int32_t *h, const uint8_t *alpha_in /* d*q */,
+                     uint8_t *beta_out /* d*q */) {
+  return orc_check_update_counted(q, poly, d, h, alpha_in, beta_out, NULL);
 }
 
 /* ---- decoder --------------------------------------------------------- */
@@ -203,7 +219,7 @@ int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, c
             ap[j] = alpha + (size_t)e * q;
             bp[j] = beta + (size_t)e * q;
           }
-          cnp_one_check(&g, d, hrow, ap, bp, F, B);
+          cnp_one_check(&g, d, hrow, ap, bp, F, B, NULL);
         }
         /* VNP for every variable node:
          *   alpha'_{m,n}(x) = gamma_n(x) + sum over i in S_c(n)\m of beta_{i,n}(x)

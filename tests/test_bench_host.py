@@ -131,6 +131,26 @@ def test_fftspa_count_against_table1(name):
     assert bench.fft_flops_per_frame_iter(code) == no_lc - dropped
 
 
+@pytest.mark.parametrize("q,d", [(4, 2), (4, 4), (8, 5), (16, 6), (64, 4)])
+def test_oracle_visits_the_pairs_the_counts_assume(q, d):
+    """The oracle's check update, instrumented, visits (d - 2) q^2 pairs in each of its forward,
+    backward and beta remaining-edge blocks: the 3(d - 2) q^2 per check of the roofline numerator.
+    Table 1 lists (d - 1) q^2 for each of F and B (its F_{d-1} and B_0 feed no message) and
+    (d - 2) q^2 for beta."""
+    import oracle
+    rng = np.random.default_rng(q * 100 + d)
+    h = rng.integers(1, q, d)
+    alpha = rng.integers(0, 64, (d, q))
+    beta, pairs = oracle.check_update_pairs(q, I.PRIMITIVE_POLY[q], h, alpha)
+    assert np.array_equal(beta, oracle.check_update(q, I.PRIMITIVE_POLY[q], h, alpha))
+    assert list(pairs) == [(d - 2) * q * q] * 3
+    code = I.code_from_dense(np.array([h]), q, I.PRIMITIVE_POLY[q])
+    assert bench.pairs_per_frame_iter(code) == int(pairs.sum())
+    rows = _table1_minmax(1, d, d, 1, q)
+    assert rows["fb_rest"][0] == pairs[0] + pairs[1] + 2 * q * q
+    assert rows["beta_rest"][0] == pairs[2]
+
+
 def test_code_hash_ignores_comments_and_layout_only():
     """The profile fingerprint: comments and whitespace do not count, code and literals do."""
     a = "int f(int x) {  // twice\n  return 2 * x; /* doubled */ }\n"
