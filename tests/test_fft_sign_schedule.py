@@ -179,3 +179,123 @@ def test_a_wrong_coefficient_is_caught(tables):
     got = kernel_model(q, DC, us, hs, T)
     want = brute_force(q, us, hs)
     assert max(np.abs(g_ - w_).max() for g_, w_ in zip(got, want)) > 1e-3
+
+
+# ---- the select-based form the select-free one replaced, in float32 -------------------------
+def _f32(x):
+    return np.float32(x)
+
+
+def wht_select_based(V, q, inverse):
+    """Register butterflies (a + b, a - b), then half exchanges with selects: the lower lane of a
+    pair keeps register r and sends r | c, the upper lane the reverse, and the upper lane negates
+    its differences; forward lane stages 0..K-1, inverse K-1..0."""
+    R = LANE_ELEMS[q]
+    RB = R.bit_length() - 1
+    G, K = q // R, q.bit_length() - 1 - RB
+    V = V.astype(np.float32).copy()
+    for b in range(RB):
+        h = 1 << b
+        for gl in range(G):
+            for r in range(R):
+                if not r & h:
+                    a, c_ = V[gl, r], V[gl, r | h]
+                    V[gl, r], V[gl, r | h] = _f32(a + c_), _f32(a - c_)
+    for s in range(K):
+        k = K - 1 - s if inverse else s
+        c = 1 << (k % RB)
+        old = V.copy()
+        for gl in range(G):
+            up = (gl >> k) & 1
+            p = gl ^ (1 << k)
+            for r in range(R):
+                if r & c:
+                    continue
+                keep = old[gl, r | c] if up else old[gl, r]
+                recv = old[p, r | c] if up else old[p, r]     # what the partner sends
+                V[gl, r] = _f32(keep + recv)
+                V[gl, r | c] = _f32((-1.0 if up else 1.0) * _f32(keep - recv))
+    return V
+
+
+def wht_sf32(V, q, masks, inverse):
+    """The select-free stages in float32: out = recv +- x * keep with one rounding (x = +-1)."""
+    R = LANE_ELEMS[q]
+    RB = R.bit_length() - 1
+    G, K = q // R, q.bit_length() - 1 - RB
+    V = V.astype(np.float32).copy()
+    for b in range(RB):
+        h = 1 << b
+        for gl in range(G):
+            x = coef(masks[b], gl)
+            for r in range(R):
+                if not r & h:
+                    keep, recv = V[gl, r], V[gl, r | h]
+                    V[gl, r], V[gl, r | h] = _f32(recv + x * keep), _f32(recv - x * keep)
+    for s in range(K):
+        k = K - 1 - s if inverse else s
+        c = 1 << (k % RB)
+        old = V.copy()
+        for gl in range(G):
+            x = coef(masks[RB + s], gl)
+            for r in range(R):
+                if not r & c:
+                    keep, recv = old[gl, r], old[gl ^ (1 << k), r | c]
+                    V[gl, r], V[gl, r | c] = _f32(recv + x * keep), _f32(recv - x * keep)
+    return V
+
+
+def check_node_f32(q, DC, us, hs, T):
+    """One check in float32 through both forms; returns (select-based, select-free) outputs."""
+    mul, inv = field(q)
+    R = LANE_ELEMS[q]
+    RB = R.bit_length() - 1
+    G, K = q // R, q.bit_length() - 1 - RB
+    d = len(us)
+    y0 = np.arange(G) * R
+    y0s = y0 ^ (np.arange(G) & ((1 << min(K, RB)) - 1))
+    outs = []
+    for select_free in (False, True):
+        base = y0s if select_free else y0
+        W = np.ones((DC, G, R), np.float32)
+        pad = np.ones((G, R), np.float32)
+        if select_free and d < DC and (DC - d) % 2:
+            pad = np.zeros((G, R), np.float32)
+            pad[y0s == 0, 0] = 1.0
+            pad = wht_sf32(pad, q, T["fwd"], False)
+        for j in range(d):
+            hi = inv[hs[j]]
+            V = np.array([[us[j][mul(hi, int(base[gl]) ^ i)] for i in range(R)] for gl in range(G)], np.float32)
+            W[j] = wht_sf32(V, q, T["fwd"], False) if select_free else wht_select_based(V, q, False)
+        if d < DC:
+            W[d] = pad
+        res = []
+        for j in range(d):
+            t = np.ones((G, R), np.float32)
+            for k in range(DC):                 # the kernel's product order: k = 0..DC-1, skipping j
+                if k != j:
+                    t = (t * W[k]).astype(np.float32)
+            v = wht_sf32(t, q, T["inv"], True) if select_free else wht_select_based(t, q, True)
+            hi = inv[hs[j]]
+            dst = np.zeros(q, np.float32)
+            for gl in range(G):
+                for i in range(R):
+                    tt = _f32(v[gl, i] * coef(T["out"][i], gl)) if select_free else v[gl, i]
+                    dst[mul(hi, int(y0[gl]) ^ i)] = max(_f32(tt * np.float32(1.0 / q)), np.float32(0.0))
+            res.append(dst)
+        outs.append(res)
+    return outs
+
+
+@pytest.mark.parametrize("q", [8, 16, 32, 64, 128, 256])
+def test_select_free_outputs_are_bit_identical_in_float32(tables, q):
+    """Each select-free butterfly output is +- the select-based one with the same single rounding,
+    so after the signs are folded back the check-node outputs agree bit for bit."""
+    rng = np.random.default_rng(q + 7)
+    for DC, d in ((4, 4), (4, 3), (8, 5), (8, 8)):
+        us = [rng.random(q).astype(np.float32) for _ in range(d)]
+        us = [(u / u.sum()).astype(np.float32) for u in us]
+        hs = [int(rng.integers(1, q)) for _ in range(d)]
+        old, new = check_node_f32(q, DC, us, hs, tables[q])
+        for a, b in zip(old, new):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (q, DC, d)
