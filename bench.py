@@ -11,6 +11,13 @@ before the timed region; they are larger than L2, so no flush is needed.
 Prints one JSON line (rank 0).  With torchrun, every rank decodes its own
 batch (weak scaling, no data-path collective); the timing is the max over
 ranks.  --impl reference times the CPU oracle on the host cores instead.
+
+At N=1 the line also carries: the integer min/max peak measured by the
+throughput probe (the roofline's denominator), one sub-line per other
+min-max workload (GF(4) N=48: 1000 frames, 10 fixed iterations, plain and
+CUDA-graph replayed; GF(256) (2,6) N=384: 16384 frames, up to 20 iterations),
+the four-code persistent batch against the plain decoder, and a short
+serving sweep.
 """
 from __future__ import annotations
 
@@ -18,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -55,8 +63,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="gf64", choices=["gf64", "mixed", "serving", "width", "fftspa", "schedule"],
-                    help="gf64: the GF(64) N=576 headline step; mixed: the four-code batch, persistent vs "
+    ap.add_argument("--workload", default="gf64",
+                    choices=["gf64", "gf4", "gf256", "peak", "mixed", "serving", "width", "fftspa", "schedule"],
+                    help="gf64: the GF(64) N=576 headline step; gf4: GF(4) N=48, 1000 frames, 10 fixed "
+                         "iterations (plain and CUDA-graph replayed); gf256: GF(256) (2,6) N=384, 16384 frames; "
+                         "peak: the integer min/max throughput probe; mixed: the four-code batch, persistent vs "
                          "plain; serving: Poisson request arrivals, continuous batching vs plain; width: 8-bit "
                          "against 16-bit messages (throughput and frame error rate); fftspa: the GF(64) step "
                          "decoded with FFT-SPA (Alg. 1) from float channel probabilities; schedule: 3(d_c-2) "
@@ -66,6 +77,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default layout / frames per block")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line: skip the probe, the other workloads, the mixed batch and serving")
+    ap.add_argument("--probe-seconds", type=float, default=0.6, help="peak: seconds per probe form")
     return ap.parse_args()
 
 
@@ -172,27 +186,54 @@ class ClockSampler:
 
 
 def make_inputs(code, w, frames_per_point, device, rank):
-    from paper_2508_03567_gb300 import inputs as I
-    parts = []
-    for i, eb in enumerate(w["ebn0"]):
-        seed = I.workload_seed(WORKLOAD, i) + 7919 * rank
-        parts.append(I.make_batch(code, eb, seed, frames_per_point, device=device, chunk=8192).gamma)
-    return torch.cat(parts, 0).contiguous()
+    return make_inputs_cw(code, w, frames_per_point, device, rank)[0]
 
 
-def cpu_oracle_rate(code, w, sample_per_point, threads):
-    """Info Mbit/s of the CPU oracle on a bounded sample of the same workload."""
+def cpu_model() -> str:
+    """CPU model string of this host (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(name, frames_per_point, threads):
+    """Info Mbit/s of the CPU oracle on a bounded sample of workload `name` (the
+    first frames of each Eb/N0 point's stream), with `threads` threads."""
     import oracle
     from paper_2508_03567_gb300 import inputs as I
-    gam = []
-    for i, eb in enumerate(w["ebn0"]):
-        gam.append(I.make_batch(code, eb, I.workload_seed(WORKLOAD, i), sample_per_point).gamma.numpy())
-    g = np.concatenate(gam, 0)
+    w = I.WORKLOADS[name]
+    code = I.workload_code(name)
+    g = np.concatenate([I.make_batch(code, eb, I.workload_seed(name, i), frames_per_point).gamma.numpy()
+                        for i, eb in enumerate(w["ebn0"])], 0)
     t0 = time.perf_counter()
     oracle.decode(code, g, w["max_iters"], w["early_stop"], threads=threads)
     dt = time.perf_counter() - t0
-    bits = g.shape[0] * code.k * code.p
-    return bits / dt / 1e6, dt, g.shape[0]
+    return g.shape[0] * code.k * code.p / dt / 1e6, dt, g.shape[0]
+
+
+def cpu_baseline(name, frames_all, frames_single):
+    """The oracle as it stands, on this host: all cores (a thread pool over
+    frames) and one thread, each on a bounded sample of the workload."""
+    threads = os.cpu_count() or 1
+    rate, dt, f = oracle_rate(name, frames_all, threads)
+    rate1, dt1, f1 = oracle_rate(name, frames_single, 1)
+    return {"value": rate, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"{f} frames ({frames_all} per Eb/N0 point) of the same workload, {dt:.1f} s wall",
+            "single_thread": {"value": rate1, "unit": "Mbit/s", "cores": 1,
+                              "sample": f"{f1} frames ({frames_single} per Eb/N0 point), {dt1:.1f} s wall"},
+            "nproc": threads, "cpu_model": cpu_model(), "machine": platform.machine()}
 
 
 def run_reference(args, ws, rank):
@@ -204,10 +245,10 @@ def run_reference(args, ws, rank):
     threads = os.cpu_count() or 1
     sample = 8
     for _ in range(args.warmup):
-        cpu_oracle_rate(code, w, 2, threads)
+        oracle_rate(WORKLOAD, 2, threads)
     times, bits = [], 0
     for _ in range(args.steps):
-        rate, dt, f = cpu_oracle_rate(code, w, sample, threads)
+        rate, dt, f = oracle_rate(WORKLOAD, sample, threads)
         times.append(dt)
         bits += f * code.k * code.p
     value = bits / sum(times) / 1e6
@@ -218,7 +259,8 @@ def run_reference(args, ws, rank):
             "config": {"workload": WORKLOAD, "frames_per_step": 3 * sample, "max_iters": w["max_iters"],
                        "early_stop": True, "ebn0_db": list(w["ebn0"])},
             "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{sample} frames per Eb/N0 point per step (of 65536)"},
+                             "sample": f"{sample} frames per Eb/N0 point per step (of 65536)",
+                             "nproc": threads, "cpu_model": cpu_model(), "machine": platform.machine()},
             "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -238,9 +280,209 @@ def pairs_per_frame_iter(code):
     return convolutions_per_frame_iter(code) * code.q * code.q
 
 
-def run_mixed(args, ws, rank, local):
+# ---------------------------------------------------------------- integer peak
+# Probe forms (nbldpc_probe_minmax): the instruction mixes of the convolution's
+# inner loop on registers, and the convolution itself on shared memory.
+PROBE_FORMS = (("alu", 0), ("fma_1_8", 1), ("fma_3_8", 2), ("fma_4_8", 3), ("fma_3_8_shfl", 4))
+CONV_FORMS = (("conv_gf64", 5), ("conv_gf256", 6))
+
+
+def sm_count(dev) -> int:
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def run_probe_form(binding, form, seconds, dev, stream):
+    """One probe launch of about `seconds` (the round count calibrated on shorter launches)."""
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rounds, cap = 64, 1 << 26
+    for _ in range(10):
+        a.record(stream)
+        binding.nbldpc_probe_minmax(form, rounds, sink, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        if ms >= 0.5e3 * seconds or rounds >= cap:
+            break
+        rounds = int(min(cap, rounds * max(2.0, 1e3 * seconds / max(ms, 1e-3))))
+    a.record(stream)
+    pairs, blocks = binding.nbldpc_probe_minmax(form, rounds, sink, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    return {"pairs_per_s": pairs / (ms / 1e3), "ms": ms, "rounds": rounds, "blocks": blocks}
+
+
+def measure_peak(binding, dev, local, seconds, forms=PROBE_FORMS + CONV_FORMS):
+    """Min-max pairs per clock per SM of each probe form, using the SM clock
+    sampled while the probes ran (time x median MHz); the best register form
+    is the integer peak of the roofline."""
+    stream = torch.cuda.Stream(device=dev)
+    sms = sm_count(dev)
+    res = {}
+    with ClockSampler(local) as clk:
+        for label, form in forms:
+            res[label] = run_probe_form(binding, form, seconds, dev, stream)
+    clocks = clk.summary() or {}
+    mhz = clocks.get("sm_mhz") or sm_max_mhz()[0]
+    for r in res.values():
+        r["pairs_per_clk_sm"] = r["pairs_per_s"] / (sms * mhz * 1e6)
+    reg = [lab for lab, _ in PROBE_FORMS if lab in res]
+    best = max(reg, key=lambda k: res[k]["pairs_per_clk_sm"])
+    return {"forms": res, "best_form": best, "pairs_per_clk_sm": res[best]["pairs_per_clk_sm"], "sms": sms,
+            "clock_mhz_used": mhz, "clocks": clocks}
+
+
+def alu_peaks(peak_meas, dev):
+    """(measured peak Gop/s, its description, issue-bound peak Gop/s) in 16-bit min/max ops
+    (a min-max pair = 2 ops), both at the maximum SM clock."""
+    mhz, mhz_kind = sm_max_mhz()
+    sms = sm_count(dev)
+    issue = sms * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
+    if not peak_meas:
+        return issue, (f"derived: {sms} SMs x {PEAK_OPS_PER_CLK_SM} u16 min/max ops/clk (issue-bound ALU+FMA "
+                       f"mix) x {mhz:.0f} MHz ({mhz_kind} max SM clock)"), issue
+    ppc = peak_meas["pairs_per_clk_sm"]
+    meas = sms * 2 * ppc * mhz * 1e6 / 1e9
+    return meas, (f"measured: probe form {peak_meas['best_form']} at {ppc:.1f} min-max pairs/clk/SM "
+                  f"(x 2 u16 ops) x {sms} SMs x {mhz:.0f} MHz ({mhz_kind} max SM clock)"), issue
+
+
+def roofline_alu(achieved, peak, peak_kind, issue, traffic=None):
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "peak_issue_bound": issue,
+            "frac_issue_bound": achieved / issue}
+
+
+def run_peak(args, ws, rank, local):
+    """Every probe form for --probe-seconds each: min-max pairs per clock per SM."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    meas = measure_peak(binding, dev, local, args.probe_seconds)
+    peak, kind, issue = alu_peaks(meas, dev)
+    line = {"metric": "integer min/max throughput (min-max pairs per clock per SM)",
+            "value": meas["pairs_per_clk_sm"], "unit": "pairs/clk/SM", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16x2", "data": "synthetic",
+            "config": {"workload": "throughput probe of the convolution's instruction forms",
+                       "seconds_per_form": args.probe_seconds},
+            "peak_gops": peak, "peak_kind": kind, "issue_bound_gops": issue, "probe": meas,
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- one min-max workload
+def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, frames=None, graph_repeat=0,
+                     cpu_frames=None, e2e=True, profile=None):
+    """One min-max workload of inputs.WORKLOADS through nbldpc_decode: its frames
+    at every Eb/N0 point (inputs resident in HBM), `warmup` untimed and `steps`
+    timed decodes (CUDA events on the launching stream), info Mbit/s, frame
+    error rate against the transmitted codewords, the ALU roofline, clocks,
+    and optionally a CUDA-graph replay of `graph_repeat` decodes, the e2e
+    host-buffer decode and the CPU oracle on a sample."""
+    w = I.WORKLOADS[name]
+    code = I.workload_code(name)
+    fpp = frames or w["frames"]
+    gam, cws = [], []
+    for i, eb in enumerate(w["ebn0"]):
+        b = I.make_batch(code, eb, I.workload_seed(name, i), fpp, device=dev, chunk=8192)
+        gam.append(b.gamma)
+        cws.append(b.codewords)
+    gamma = torch.cat(gam, 0).contiguous()
+    cw = torch.cat(cws, 0)
+    del gam, cws
+    nf = gamma.shape[0]
+    dec = binding.Decoder.from_code(code)
+    tuning = {"source": "default"}
+    if not args.no_autotune:
+        res = dec.autotune(gamma[: min(nf, 4096)], 3)
+        tuning = {"source": "autotuned", "candidates_ms": {f"v{v}_fpb{f}": round(ms, 3) for v, f, ms in res}}
+    v, fpb = dec.tuning()
+    tuning.update({"variant": v, "frames_per_block": fpb})
+    stream = torch.cuda.Stream(device=dev)
+    sym = torch.empty((nf, code.n), dtype=torch.uint8, device=dev)
+    its = torch.empty((nf,), dtype=torch.int32, device=dev)
+    ok = torch.empty((nf,), dtype=torch.uint8, device=dev)
+    wsb = dec.workspace(nf, dev)
+    mi, es = w["max_iters"], w["early_stop"]
+
+    def step():
+        binding.nbldpc_decode(dec.handle, gamma, nf, mi, es, sym, its, ok, wsb, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = binding.nbldpc_kernel_launch_count()
+    with ClockSampler(local) as clk:
+        for a, b in ev:
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    launches = binding.nbldpc_kernel_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kernel_s = statistics.mean(step_ms) / 1e3
+    its_h = its.cpu().numpy().astype(np.int64)
+    pairs_step = int(its_h.sum()) * pairs_per_frame_iter(code)
+    achieved = 2 * pairs_step / kernel_s / 1e9
+    peak, kind, issue = peaks
+    bpf = profiled_traffic(profile)[0] if profile else None
+    info_bits = nf * code.k * code.p
+    out = {"workload": name, "value": info_bits / kernel_s / 1e6, "unit": "Mbit/s", "steps": steps,
+           "warmup": warmup, "ms_per_step": 1e3 * kernel_s, "median_ms_per_step": statistics.median(step_ms),
+           "config": {"q": code.q, "n": code.n, "k": code.k, "dv": w["dv"], "dc": w["dc"], "frames_per_step": nf,
+                      "ebn0_db": list(w["ebn0"]), "max_iters": mi, "early_stop": bool(es), "tuning": tuning,
+                      "l2": "inputs larger than L2 (no flush)" if gamma.numel() > 129e6 else
+                            "inputs smaller than L2: resident across steps"},
+           "roofline": roofline_alu(achieved, peak, kind, issue, None if bpf is None else bpf * nf),
+           "clocks": clk.summary(), "gpu_launches": int(launches),
+           "fer": float((sym.to(torch.int64) != cw).any(1).float().mean()),
+           "not_ok": float(1 - ok.float().mean()), "mean_iters": float(its_h.mean()),
+           "pairs_per_step": pairs_step, "coded_mbps": info_bits / kernel_s / 1e6 * code.n / code.k}
+    if graph_repeat:
+        # the same decode captured `graph_repeat` times in one CUDA graph: launch cost off the host
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(graph_repeat):
+                step()
+        def replay():
+            with torch.cuda.stream(stream):
+                graph.replay()
+        for _ in range(2):
+            replay()
+        torch.cuda.synchronize()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in gev:
+            a.record(stream)
+            replay()
+            b.record(stream)
+        torch.cuda.synchronize()
+        per = sum(a.elapsed_time(b) for a, b in gev) / (steps * graph_repeat) / 1e3
+        gp = int(its.cpu().numpy().astype(np.int64).sum()) * pairs_per_frame_iter(code)
+        out["graph"] = {"value": info_bits / per / 1e6, "unit": "Mbit/s", "ms_per_decode": 1e3 * per,
+                        "decodes_per_replay": graph_repeat, "replays": steps,
+                        "roofline": roofline_alu(2 * gp / per / 1e9, peak, kind, issue),
+                        "form": f"{graph_repeat} nbldpc_decode calls captured in one CUDA graph, replayed"}
+    if e2e and not args.no_e2e:
+        out["e2e"] = measure_e2e(binding, dec, code, gamma, mi, es, args, dev)
+    if cpu_frames and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(name, *cpu_frames)
+    del gamma
+    return out
+
+
+def run_mixed(args, ws, rank, local, emit=True, steps=None, warmup=None, peaks=None):
     """Four codes in one persistent launch (graph-replayed) against one
-    fixed-iteration launch per code (the plain batch decoder)."""
+    fixed-iteration launch per code (the plain batch decoder).  With emit=False
+    the line is returned instead of printed."""
     import __graft_entry__
     __graft_entry__.build()
     from paper_2508_03567_gb300 import binding, inputs as I
@@ -262,6 +504,8 @@ def run_mixed(args, ws, rank, local):
         outs.append((torch.empty((f, code.n), dtype=torch.uint8, device=dev),
                      torch.empty((f,), dtype=torch.int32, device=dev),
                      torch.empty((f,), dtype=torch.uint8, device=dev)))
+    steps = steps or steps
+    warmup = warmup or warmup
     jobs = [(d.handle, g, g.shape[0], max_iters, 1, *o) for d, g, o in zip(decs, gam, outs)]
     wsb = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -282,7 +526,7 @@ def run_mixed(args, ws, rank, local):
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
     # persistent mixed batch, captured once and replayed
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         binding.nbldpc_decode_batch(jobs, wsb, stream=stream)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -292,7 +536,7 @@ def run_mixed(args, ws, rank, local):
         with torch.cuda.stream(stream):
             graph.replay()
     with ClockSampler(local) as clk:
-        t_pers = timed(replay, args.steps)
+        t_pers = timed(replay, steps)
     its_pers = [o[1].cpu().numpy().astype(np.int64) for o in outs]
     fer_pers = fer_of([o[0] for o in outs])
     pairs = sum(int(it.sum()) * pairs_per_frame_iter(c) for it, c in zip(its_pers, codes))
@@ -302,50 +546,52 @@ def run_mixed(args, ws, rank, local):
         for d, g, (sym, its, ok) in zip(decs, gam, outs):
             binding.nbldpc_decode(d.handle, g, g.shape[0], max_iters, early, sym, its, ok,
                                   d.workspace(g.shape[0], dev), stream=stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain(0)
-    t_fixed = timed(lambda: plain(0), args.steps)
+    t_fixed = timed(lambda: plain(0), steps)
     fer_fixed = fer_of([o[0] for o in outs])
     for _ in range(2):
         plain(1)
-    t_early = timed(lambda: plain(1), args.steps)
-    mhz, mhz_kind = sm_max_mhz()
-    peak = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
-    achieved = 2 * pairs / (t_pers / args.steps) / 1e9
+    t_early = timed(lambda: plain(1), steps)
+    peak, kind, issue = peaks or alu_peaks(None, dev)
+    achieved = 2 * pairs / (t_pers / steps) / 1e9
     if rank != 0:
         return 0
     line = {
-        "metric": "decoded info Mbit/s", "value": ws * args.steps * info_bits / t_pers / 1e6, "unit": "Mbit/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_pers / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": "decoded info Mbit/s", "value": ws * steps * info_bits / t_pers / 1e6, "unit": "Mbit/s",
+        "n_gpus": ws, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * t_pers / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "mixed4: GF(16) N=1024 (2,4) + GF(64) N=576 (2,4) + GF(32) N=600 (3,6) "
                                "+ GF(256) N=128 (2,8)", "frames": dict(zip(I.MIXED_SET, counts)),
                    "ebn0_db": "uniform per frame in [1.5, 3.5)", "max_iters": max_iters,
                    "form": "one persistent launch per step (CUDA graph replay), early stop + refill",
                    "tuning": tuning},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": None},
+        "roofline": roofline_alu(achieved, peak, kind, issue),
         "clocks": clk.summary(),
-        "gpu_launches": args.steps,   # one decode kernel per graph replay
+        "gpu_launches": steps,   # one decode kernel per graph replay
         "fer": fer_pers,
-        "plain_fixed_iterations": {"value": ws * args.steps * info_bits / t_fixed / 1e6, "unit": "Mbit/s",
-                                   "ms_per_step": 1e3 * t_fixed / args.steps, "fer": fer_fixed,
+        "plain_fixed_iterations": {"value": ws * steps * info_bits / t_fixed / 1e6, "unit": "Mbit/s",
+                                   "ms_per_step": 1e3 * t_fixed / steps, "fer": fer_fixed,
                                    "form": "one launch per code, 30 iterations, no early stop"},
-        "plain_early_stop": {"value": ws * args.steps * info_bits / t_early / 1e6, "unit": "Mbit/s",
-                             "ms_per_step": 1e3 * t_early / args.steps,
+        "plain_early_stop": {"value": ws * steps * info_bits / t_early / 1e6, "unit": "Mbit/s",
+                             "ms_per_step": 1e3 * t_early / steps,
                              "form": "one launch per code, early stop"},
         "mean_iters": {c.name: float(it.mean()) for c, it in zip(codes, its_pers)},
     }
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args, ws, rank, local):
+def run_serving(args, ws, rank, local, emit=True, loads_c=(0.10, 0.25, 0.50, 0.75, 0.90, 1.00),
+                loads_p=(0.10, 0.25, 0.50), seconds=None):
     """Poisson arrivals of requests (one of the four mixed-set codes, uniform;
     1-256 frames, uniform; per-frame Eb/N0 uniform in [1.5, 3.5) dB) served by
     continuous batching, load swept over fractions of the measured peak, and
-    by the plain one-launch-per-request decoder."""
+    by the plain one-launch-per-request decoder.  With emit=False the line is
+    returned instead of printed."""
     import __graft_entry__
     __graft_entry__.build()
     from paper_2508_03567_gb300 import binding, inputs as I
@@ -411,13 +657,14 @@ def run_serving(args, ws, rank, local):
     peak_plain = serve("plain", 0, 0, 3, saturate=True)
     peak_bps = peak["achieved_mbps"] * 1e6
     loads = []
-    for i, load in enumerate((0.10, 0.25, 0.50, 0.75, 0.90, 1.00)):
-        res = serve("continuous", load * peak_bps / mean_bits, args.seconds, 5000 + i)
+    seconds = seconds or args.seconds
+    for i, load in enumerate(loads_c):
+        res = serve("continuous", load * peak_bps / mean_bits, seconds, 5000 + i)
         res["load"] = load
         loads.append(res)
     plain = []
-    for i, load in enumerate((0.10, 0.25, 0.50)):
-        res = serve("plain", load * peak_bps / mean_bits, args.seconds, 5100 + i, cap=20.0)
+    for i, load in enumerate(loads_p):
+        res = serve("plain", load * peak_bps / mean_bits, seconds, 5100 + i, cap=20.0)
         res["load"] = load
         plain.append(res)
     line = {"metric": "decoded info Mbit/s; p50/p99 request latency", "value": peak["achieved_mbps"],
@@ -430,6 +677,8 @@ def run_serving(args, ws, rank, local):
                        "streams": 3, "max_requests_per_launch": 32},
             "peak_continuous": peak, "peak_plain": peak_plain, "loads_continuous": loads,
             "loads_plain": plain}
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
@@ -751,6 +1000,46 @@ def run_schedule(args, ws, rank, local):
     return 0
 
 
+def make_inputs_cw(code, w, frames_per_point, device, rank):
+    """The headline step's reliabilities and transmitted codewords (rank-specific seeds)."""
+    from paper_2508_03567_gb300 import inputs as I
+    gam, cws = [], []
+    for i, eb in enumerate(w["ebn0"]):
+        seed = I.workload_seed(WORKLOAD, i) + 7919 * rank
+        b = I.make_batch(code, eb, seed, frames_per_point, device=device, chunk=8192)
+        gam.append(b.gamma)
+        cws.append(b.codewords)
+    return torch.cat(gam, 0).contiguous(), torch.cat(cws, 0)
+
+
+def run_single(args, ws, rank, local, name, graph_repeat=0, cpu_frames=None, profile=None):
+    """--workload gf4 / gf256: one min-max workload as its own line."""
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_03567_gb300 import binding, inputs as I
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peaks = alu_peaks(None if args.no_extras else measure_peak(binding, dev, local, 0.3, PROBE_FORMS), dev)
+    r = measure_workload(binding, I, name, dev, local, args, peaks, args.steps, args.warmup,
+                         frames=args.frames, graph_repeat=graph_repeat, cpu_frames=cpu_frames, profile=profile)
+    line = {"metric": "decoded info Mbit/s", "value": r.pop("value"), "unit": "Mbit/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": dict(workload=name, **r.pop("config")), **r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# workloads beside the headline: (name, graph-replay repeat, CPU sample (all cores, one thread) per Eb/N0
+# point, committed ncu summary)
+SIDE_WORKLOADS = (("gf4_n48_dv2_dc4", 100, (1000, 1000), "mma_decode_kernel_gf4_n48.md"),
+                  ("gf256_n384_dv2_dc6", 0, (16, 2), "mma_decode_kernel_gf256_n384.md"))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -766,6 +1055,11 @@ def main():
         return run_fftspa(args, ws, rank, local)
     if args.workload == "schedule":
         return run_schedule(args, ws, rank, local)
+    if args.workload == "peak":
+        return run_peak(args, ws, rank, local)
+    if args.workload in ("gf4", "gf256"):
+        name, rep, cpuf, prof = SIDE_WORKLOADS[0 if args.workload == "gf4" else 1]
+        return run_single(args, ws, rank, local, name, rep, cpuf, prof)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     import __graft_entry__
@@ -776,7 +1070,11 @@ def main():
     fpp = args.frames or w["frames"]
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    gamma = make_inputs(code, w, fpp, dev, rank)
+    extras = ws == 1 and not args.no_extras
+    # the integer min/max peak of this GPU, measured before the timed region (probe kernels)
+    peak_meas = measure_peak(binding, dev, local, args.probe_seconds) if extras else None
+    peaks = alu_peaks(peak_meas, dev)
+    gamma, cw = make_inputs_cw(code, w, fpp, dev, rank)
     frames = gamma.shape[0]
     dec = binding.Decoder.from_code(code)
     tuning = {"source": "default"}
@@ -825,16 +1123,15 @@ def main():
     # decode statistics and algorithmic work of one step (identical every step)
     its_h = its.cpu().numpy().astype(np.int64)
     ok_h = ok.cpu().numpy()
-    pairs_fi = code.m * 3 * (w["dc"] - 2) * code.q * code.q   # min-max pairs per frame-iteration
-    pairs_step = int(its_h.sum()) * pairs_fi
+    fer = float((sym.to(torch.int64) != cw).any(1).float().mean())
+    pairs_step = int(its_h.sum()) * pairs_per_frame_iter(code)
     info_bits_step = frames * code.k * code.p
     value = ws * args.steps * info_bits_step / total_s / 1e6
     kernel_s = statistics.mean(step_ms) / 1e3
     median_ms = statistics.median(step_ms)
     achieved_gops = 2 * pairs_step / kernel_s / 1e9           # 16-bit min/max ops per second
     clocks = clk.summary()
-    mhz, mhz_kind = sm_max_mhz()
-    peak_gops = SM_COUNT * PEAK_OPS_PER_CLK_SM * mhz * 1e6 / 1e9
+    peak_gops, peak_kind, issue_gops = peaks
     bpf, _ = profiled_traffic()
 
     e2e = None
@@ -842,10 +1139,37 @@ def main():
         e2e = measure_e2e(binding, dec, code, gamma, mi, es, args, dev)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        threads = os.cpu_count() or 1
-        rate, dt, f = cpu_oracle_rate(code, w, 64, threads)
-        cpu = {"value": rate, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
-               "sample": f"{f} frames (64 per Eb/N0 point) of the same workload, {dt:.1f} s wall"}
+        cpu = cpu_baseline(WORKLOAD, 64, 4)
+    del gamma, cw, sym
+    torch.cuda.empty_cache()
+
+    side, mixed, serving = None, None, None
+    if extras and rank == 0:
+        ks, kw = min(args.steps, 5), 3
+        side = {}
+        for name, rep, cpuf, prof in SIDE_WORKLOADS:
+            side[name] = measure_workload(binding, I, name, dev, local, args, peaks, ks, kw, graph_repeat=rep,
+                                          cpu_frames=cpuf, profile=prof)
+            torch.cuda.empty_cache()
+        # GF(4) N=48 at a batch large enough that launch cost does not dominate (kernel rate)
+        big = measure_workload(binding, I, "gf4_n48_dv2_dc4", dev, local, args, peaks, ks, kw, frames=262144,
+                               e2e=False)
+        side["gf4_n48_dv2_dc4"]["kernel_rate_262144_frames"] = {
+            k: big[k] for k in ("value", "unit", "ms_per_step", "roofline", "fer", "mean_iters", "clocks")}
+        m = run_mixed(args, ws, rank, local, emit=False, steps=ks, warmup=kw, peaks=peaks)
+        mixed = {"value": m["value"], "unit": "Mbit/s", "ms_per_step": m["ms_per_step"], "fer": m["fer"],
+                 "roofline_frac": m["roofline"]["frac"], "form": m["config"]["form"],
+                 "plain_fixed_iterations": m["plain_fixed_iterations"], "plain_early_stop": m["plain_early_stop"],
+                 "frames": m["config"]["frames"], "clocks": m["clocks"]}
+        torch.cuda.empty_cache()
+        sv = run_serving(args, ws, rank, local, emit=False, loads_c=(0.10, 0.50), loads_p=(0.10,), seconds=3.0)
+        serving = {"saturated_mbps": sv["peak_continuous"]["achieved_mbps"],
+                   "plain_saturated_mbps": sv["peak_plain"]["achieved_mbps"],
+                   "loads": [{k: r[k] for k in ("load", "offered_mbps", "achieved_mbps", "p50_ms", "p99_ms",
+                                                  "requests", "completed")} for r in sv["loads_continuous"]],
+                   "plain_loads": [{k: r[k] for k in ("load", "offered_mbps", "achieved_mbps", "p50_ms", "p99_ms",
+                                                        "requests", "completed")} for r in sv["loads_plain"]],
+                   "form": "native server, continuous batching, 3 s Poisson window per load point"}
 
     if rank != 0:
         return 0
@@ -858,20 +1182,23 @@ def main():
                    "k": code.k, "dv": w["dv"], "dc": w["dc"], "ebn0_db": list(w["ebn0"]),
                    "max_iters": mi, "early_stop": bool(es), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"frames sharded over {ws} GPU(s)", "tuning": tuning},
-        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved_gops / peak_gops,
-                     "traffic": None if bpf is None else bpf * frames,
-                     "peak_kind": f"derived: 152 SMs x 256 u16 min/max ops/clk (issue-bound ALU+FMA mix) x {mhz:.0f} MHz ({mhz_kind} max SM clock)"},
+        "roofline": roofline_alu(achieved_gops, peak_gops, peak_kind, issue_gops,
+                                 None if bpf is None else bpf * frames),
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "decode_stats": {"mean_iters": float(its_h.mean()), "fer_proxy_not_ok": float(1 - ok_h.mean()),
+        "fer": fer,
+        "decode_stats": {"mean_iters": float(its_h.mean()), "not_ok": float(1 - ok_h.mean()),
                          "pairs_per_step": pairs_step, "kernel_ms": 1e3 * kernel_s,
                          "median_ms_per_step": median_ms,
                          "wall_ms_per_step": 1e3 * (t1 - t0) / args.steps},
         # the paper's throughput formula counts coded bits (N p per frame)
         "coded_mbps": value * code.n / code.k,
+        "integer_peak_probe": peak_meas,
+        "configs": side,
+        "mixed": mixed,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0

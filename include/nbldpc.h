@@ -34,7 +34,14 @@
 extern "C" {
 #endif
 
-typedef struct nbldpc_code nbldpc_code; /* opaque; immutable after create */
+/*
+ * Opaque code handle.  The code (H and its field) is fixed at create; the
+ * launch configuration (tuning, message width, check-node schedule) changes
+ * only through nbldpc_code_set_tuning, nbldpc_code_set_message_bits,
+ * nbldpc_code_set_cnp_schedule and nbldpc_code_autotune, which must not run
+ * concurrently with any other call on the same handle.
+ */
+typedef struct nbldpc_code nbldpc_code;
 
 enum {
   NBLDPC_OK = 0,
@@ -72,9 +79,12 @@ enum {
  *
  * The handle owns device copies of H, its variable-node view and the GF
  * exponent/logarithm tables, allocated on the device that is current at this
- * call; decode on that device.  Copies the host arrays; the caller keeps
- * ownership of them.  Thread safe for concurrent decodes that use distinct
- * workspaces.
+ * call; every later call that queues GPU work on the handle returns
+ * NBLDPC_ERR_ARG (before queueing anything) unless that device is current.
+ * Copies the host arrays; the caller keeps ownership of them.  Decodes may run
+ * concurrently from several threads on one handle when each uses its own
+ * workspace; the setters and the autotuner may not run alongside any other
+ * call on the handle.
  */
 int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const int32_t *row_ptr,
                        const int32_t *col_idx, const uint8_t *coef, nbldpc_code **out);
@@ -200,7 +210,8 @@ typedef struct nbldpc_tune_result {
 
 int nbldpc_code_get_tuning(const nbldpc_code *code, int *variant, int *frames_per_block);
 
-/* Set the tuning by hand; NBLDPC_ERR_UNSUPPORTED if that pair does not fit the device. */
+/* Set the tuning by hand; NBLDPC_ERR_UNSUPPORTED if that pair does not fit the device.  Not
+ * concurrent with any other call on the same handle (a decode reads the tuning). */
 int nbldpc_code_set_tuning(nbldpc_code *code, int variant, int frames_per_block);
 
 /* Device workspace nbldpc_code_autotune needs for `frames` tuning frames. */
@@ -231,7 +242,8 @@ int nbldpc_code_autotune(nbldpc_code *code, const uint8_t *gamma_dev, int frames
  * workspace doubles at 16 bits; mixed-code batches accept 8-bit codes only
  * (NBLDPC_ERR_UNSUPPORTED otherwise).
  */
-int nbldpc_code_set_message_bits(nbldpc_code *code, int bits);   /* bits: 8 or 16 */
+/* bits: 8 or 16.  Not concurrent with any other call on the same handle. */
+int nbldpc_code_set_message_bits(nbldpc_code *code, int bits);
 int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
 
 /*
@@ -248,6 +260,7 @@ int nbldpc_code_get_message_bits(const nbldpc_code *code, int *bits);
  */
 #define NBLDPC_CNP_MINIMAL 0
 #define NBLDPC_CNP_TABLE1 1
+/* Not concurrent with any other call on the same handle. */
 int nbldpc_code_set_cnp_schedule(nbldpc_code *code, int schedule);
 int nbldpc_code_get_cnp_schedule(const nbldpc_code *code, int *schedule);
 
@@ -351,10 +364,11 @@ int nbldpc_fftspa_decode_host(const nbldpc_code *code, const float *prob_host, i
  * lower throughput).  A code whose slot alone exceeds the array is rejected
  * with NBLDPC_ERR_UNSUPPORTED before anything is queued.
  *
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Nothing is allocated by this function: no cudaMalloc, no
- * cudaFree, no allocating library routine.
+ * Every call looks up the array's address in the current device's context
+ * (cudaGetSymbolAddress), so it stays valid across a context reset; the first
+ * call on a device may load the library's device code there, so make that
+ * first call before any stream capture.  Nothing is allocated by this
+ * function: no cudaMalloc, no cudaFree, no allocating library routine.
  *
  * All calls share the one array, and each call leaves its own contents
  * there.  Calls whose work overlaps on the GPU (different streams, different
@@ -452,6 +466,45 @@ void nbldpc_server_destroy(nbldpc_server *server);
  * was loaded (all threads, all handles).  Launch accounting for benchmarks.
  */
 uint64_t nbldpc_kernel_launch_count(void);
+
+/*
+ * ---- Measurement: integer min/max throughput probe ----------------------------
+ * The check-node pass of Alg. 2 is a chain of XOR min-max convolutions,
+ * C(x) = min_y max(A(y), B(x ^ y)) (F, B and beta equations), computed here on
+ * packed pairs of 16-bit values.  The probe runs the instruction forms of that
+ * computation alone on every SM, so that a decode's measured min-max rate can
+ * be set against the rate the hardware gives those instructions:
+ *
+ *   NBLDPC_PROBE_ALU           max.u16x2 / min.u16x2 on the integer ALU pipe
+ *   NBLDPC_PROBE_FMA_k_8       k/8 of the maxima as b + relu(a - b) on the FMA
+ *                              pipe (fma.rn.relu.f16x2 + add.rn.f16x2), the
+ *                              rest as above (the decode kernels use 3/8 for
+ *                              q <= 64 and 1/8 for q >= 128)
+ *   NBLDPC_PROBE_FMA_3_8_SHFL  the 3/8 mix with its A operands exchanged by
+ *                              shfl.xor, as in the convolution's inner loop
+ *   NBLDPC_PROBE_CONV_64/256   the decode kernels' convolution itself (GF(64)
+ *                              16-lane layout / GF(256) 32-lane layout) chained
+ *                              on shared-memory vectors
+ *
+ * Queues one launch that fills the current device (resident blocks x SMs) and
+ * runs `rounds` (>= 1) rounds per thread on `cuda_stream`; *pairs receives the
+ * min-max pairs (one 16-bit maximum + one 16-bit minimum each) the launch
+ * performs and *blocks the grid size (either may be NULL).  sink_dev: device,
+ * one unsigned int the kernel may write (it keeps the results live; its value
+ * is meaningless).  The caller times the launch (e.g. with events on the
+ * stream).  NBLDPC_ERR_ARG for an unknown form, rounds < 1 or a NULL sink.
+ */
+enum {
+  NBLDPC_PROBE_ALU = 0,
+  NBLDPC_PROBE_FMA_1_8 = 1,
+  NBLDPC_PROBE_FMA_3_8 = 2,
+  NBLDPC_PROBE_FMA_4_8 = 3,
+  NBLDPC_PROBE_FMA_3_8_SHFL = 4,
+  NBLDPC_PROBE_CONV_64 = 5,
+  NBLDPC_PROBE_CONV_256 = 6
+};
+int nbldpc_probe_minmax(int form, int rounds, unsigned int *sink_dev, double *pairs, int *blocks,
+                        void *cuda_stream);
 
 /* Static description of a status code (never NULL). */
 const char *nbldpc_status_string(int status);

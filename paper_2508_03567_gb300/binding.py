@@ -36,7 +36,7 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_fftspa_decode_host_workspace_size", "nbldpc_fftspa_decode_host",
             "nbldpc_server_create", "nbldpc_server_create_custom", "nbldpc_server_submit", "nbldpc_server_poll",
             "nbldpc_server_stats_get", "nbldpc_server_destroy",
-            "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count",
+            "nbldpc_decode_noalloc", "nbldpc_kernel_launch_count", "nbldpc_probe_minmax",
             "nbldpc_status_string")
 
 NBLDPC_MAX_BATCH_JOBS = 32
@@ -142,6 +142,8 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_code_autotune_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_code_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(nbldpc_tune_result), ctypes.c_int, ip]
+            L.nbldpc_probe_minmax.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double),
+                                              ip, vp]
             L.nbldpc_kernel_launch_count.argtypes = []
             L.nbldpc_kernel_launch_count.restype = ctypes.c_uint64
             L.nbldpc_status_string.argtypes = [ctypes.c_int]
@@ -161,6 +163,24 @@ def nbldpc_status_string(status: int) -> str:
 
 def nbldpc_kernel_launch_count() -> int:
     return int(lib().nbldpc_kernel_launch_count())
+
+
+NBLDPC_PROBE_ALU = 0
+NBLDPC_PROBE_FMA_1_8 = 1
+NBLDPC_PROBE_FMA_3_8 = 2
+NBLDPC_PROBE_FMA_4_8 = 3
+NBLDPC_PROBE_FMA_3_8_SHFL = 4
+NBLDPC_PROBE_CONV_64 = 5
+NBLDPC_PROBE_CONV_256 = 6
+
+
+def nbldpc_probe_minmax(form: int, rounds: int, sink, stream=None):
+    """Queue one min/max throughput probe launch; returns (min-max pairs of the launch, grid blocks)."""
+    pairs, blocks = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(lib().nbldpc_probe_minmax(int(form), int(rounds), ctypes.c_void_p(_ptr(sink)), ctypes.byref(pairs),
+                                     ctypes.byref(blocks), ctypes.c_void_p(_stream_ptr(stream))),
+           "nbldpc_probe_minmax")
+    return pairs.value, blocks.value
 
 
 def nbldpc_code_create(q: int, prim_poly: int, n_cols: int, n_rows: int, row_ptr, col_idx, coef) -> int:

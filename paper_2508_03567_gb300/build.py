@@ -42,6 +42,7 @@ def _units():
     units.append((os.path.join(CSRC, "nbldpc.cu"), "nbldpc.o", []))
     units.append((os.path.join(CSRC, "fftspa_host.cu"), "fftspa_host.o", []))
     units.append((os.path.join(CSRC, "server.cu"), "server.o", []))
+    units.append((os.path.join(CSRC, "probe.cu"), "probe.o", []))
     return units
 
 
@@ -66,13 +67,18 @@ def build_library(force: bool = False, verbose: bool = False, jobs: int | None =
         return out
 
     units = _units()
-    with ThreadPoolExecutor(max_workers=jobs or min(len(units), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_unit, units))
+    outs = [os.path.join(OBJ_DIR, f"{pid}_{abs(hash(tuple(extra_flags)))}_{u[1]}") for u in units]
     tmp = lib + f".{pid}.tmp"
-    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp])
-    os.replace(tmp, lib)
-    for o in objs:
-        os.remove(o)
+    try:
+        with ThreadPoolExecutor(max_workers=jobs or min(len(units), os.cpu_count() or 4)) as ex:
+            objs = list(ex.map(compile_unit, units))
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp])
+        os.replace(tmp, lib)
+    finally:
+        # this build's objects (and a half-written library) go, whether it succeeded or not
+        for o in outs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return lib
 
 

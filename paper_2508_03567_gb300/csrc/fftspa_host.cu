@@ -158,7 +158,9 @@ int nbldpc_fftspa_decode(const nbldpc_code* c, const float* prob_dev, int frames
   if (!aligned(prob_dev, 16) || !aligned(out_iters_dev, 4) || !aligned(workspace_dev, 16)) return NBLDPC_ERR_ARG;
   if (out_app_dev && !aligned(out_app_dev, 16)) return NBLDPC_ERR_ARG;
   if (workspace_bytes < ws_bytes(c->fft_plan, frames)) return NBLDPC_ERR_ARG;
-  int st = cuda_status(cudaGetLastError());
+  int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
+  st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   return fft_launch(c, prob_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, out_app_dev,
                     workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
@@ -179,6 +181,8 @@ int nbldpc_fftspa_decode_host(const nbldpc_code* cc, const float* prob_host, int
   if (!c || frames < 0 || max_iters < 0 || chunk_frames <= 0) return NBLDPC_ERR_ARG;
   if (c->fft_status != NBLDPC_OK) return c->fft_status;
   if (frames == 0) return NBLDPC_OK;
+  const int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
   const size_t fbytes = (size_t)c->n * c->q * sizeof(float);
   const size_t per = host_chunk_bytes(c, chunk_frames, fbytes, ws_bytes(c->fft_plan, chunk_frames));
   return host_chunks(c, prob_host, fbytes, frames, out_sym_host, out_iters_host, out_ok_host, chunk_frames,

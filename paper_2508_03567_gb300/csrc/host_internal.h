@@ -70,6 +70,15 @@ struct nbldpc_code {
 
 namespace nbldpc_host {
 
+// Every launch on a handle must run on the device the handle was created on:
+// its code description lives in that device's memory.  NBLDPC_ERR_ARG when
+// another device is current (checked before anything is queued).
+inline int check_device(const nbldpc_code* c) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NBLDPC_ERR_CUDA;
+  return dev == c->device ? NBLDPC_OK : NBLDPC_ERR_ARG;
+}
+
 // FFT-SPA launch shape of a code (fftspa_host.cu): NBLDPC_OK, NBLDPC_ERR_UNSUPPORTED
 // when no FFT-SPA kernel covers the code, or NBLDPC_ERR_CUDA.
 int fft_configure(nbldpc_code* c);

@@ -270,21 +270,14 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
 // Fixed scratch for callers that cannot allocate: frame counter + message slots.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NBLDPC_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {};
-
-// Device address of g_noalloc_scratch on the current device (looked up once per
-// device, with that device current; host code must not use the symbol itself).
+// Device address of g_noalloc_scratch in the current device's context.  Looked
+// up on every call (a cheap table lookup once the module is loaded), so the
+// address stays right after a context is torn down and re-created; host code
+// must not use the symbol itself, which names a host-side stand-in.
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NBLDPC_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NBLDPC_ERR_CUDA;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NBLDPC_ERR_CUDA;
+  *out = p;
   return NBLDPC_OK;
 }
 
@@ -302,13 +295,15 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
   if (!c || frames < 0 || max_iters < 0) return NBLDPC_ERR_ARG;
   if (frames == 0) return NBLDPC_OK;
   if (!valid_outputs(gamma_dev, out_sym_dev, out_iters_dev, out_ok_dev)) return NBLDPC_ERR_ARG;
+  int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
   const Plan& pl = c->plan;
   const size_t per_block = (size_t)pl.fpb * pl.slot_bytes;
   if (256 + per_block > (size_t)NBLDPC_NOALLOC_SCRATCH_BYTES) return NBLDPC_ERR_UNSUPPORTED;
   const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / per_block);
   int grid = grid_for(pl, frames);
   if (grid > fit) grid = fit;
-  int st = cuda_status(cudaGetLastError());
+  st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   void* scratch = nullptr;
   st = noalloc_scratch(&scratch);
@@ -497,12 +492,15 @@ int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
   if (!c || variant < 0 || variant > 1 || frames_per_block < 1 || frames_per_block > 8 ||
       (frames_per_block & (frames_per_block - 1)))
     return NBLDPC_ERR_ARG;
+  const int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
   return configure(c, variant, frames_per_block);
 }
 
 int nbldpc_code_set_message_bits(nbldpc_code* c, int bits) {
   if (!c || (bits != 8 && bits != 16)) return NBLDPC_ERR_ARG;
   if (bits == 16 && c->cnp_schedule == NBLDPC_CNP_TABLE1) return NBLDPC_ERR_UNSUPPORTED;
+  if (check_device(c) != NBLDPC_OK) return check_device(c);
   const int old = c->mb;
   c->mb = bits / 8;
   const int st = configure(c, c->variant, c->plan.fpb);
@@ -519,6 +517,7 @@ int nbldpc_code_get_message_bits(const nbldpc_code* c, int* bits) {
 int nbldpc_code_set_cnp_schedule(nbldpc_code* c, int schedule) {
   if (!c || (schedule != NBLDPC_CNP_MINIMAL && schedule != NBLDPC_CNP_TABLE1)) return NBLDPC_ERR_ARG;
   if (schedule == NBLDPC_CNP_TABLE1 && c->mb != 1) return NBLDPC_ERR_UNSUPPORTED;
+  if (check_device(c) != NBLDPC_OK) return check_device(c);
   const int old = c->cnp_schedule;
   c->cnp_schedule = schedule;
   const int st = configure(c, c->variant, c->plan.fpb);   // the schedule is a separate kernel
@@ -546,7 +545,9 @@ int nbldpc_decode(const nbldpc_code* c, const uint8_t* gamma_dev, int frames, in
   if (!valid_outputs(gamma_dev, out_sym_dev, out_iters_dev, out_ok_dev) || !workspace_dev) return NBLDPC_ERR_ARG;
   if (!aligned(workspace_dev, 16)) return NBLDPC_ERR_ARG;
   if (workspace_bytes < decode_ws_bytes(c, frames)) return NBLDPC_ERR_ARG;
-  int st = cuda_status(cudaGetLastError());
+  int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
+  st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   return launch(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev,
                 workspace_dev, reinterpret_cast<cudaStream_t>(cuda_stream));
@@ -561,6 +562,8 @@ static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) 
   for (int i = 0; i < n_jobs; ++i) {
     const nbldpc_code* c = jobs[i].code;
     if (!c || jobs[i].frames < 0 || jobs[i].max_iters < 0) return NBLDPC_ERR_ARG;
+    const int st = check_device(c);
+    if (st != NBLDPC_OK) return st;
     if (kmode(c) != 1) return NBLDPC_ERR_UNSUPPORTED;   // mixed-code launches: 8-bit messages, minimal schedule
     need[i] = needs_of(c, c->variant, 1);
     if (c->plan.fpb < fpb) fpb = c->plan.fpb;
@@ -632,8 +635,10 @@ int nbldpc_code_autotune(nbldpc_code* c, const uint8_t* gamma_dev, int frames, i
   if (!c || !gamma_dev || frames < 1 || max_iters < 1 || !workspace_dev || !aligned(gamma_dev, 16) ||
       !aligned(workspace_dev, 256))
     return NBLDPC_ERR_ARG;
+  int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
   size_t need = 0;
-  int st = nbldpc_code_autotune_workspace_size(c, frames, &need);
+  st = nbldpc_code_autotune_workspace_size(c, frames, &need);
   if (st != NBLDPC_OK) return st;
   if (workspace_bytes < need) return NBLDPC_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -686,6 +691,8 @@ int nbldpc_decode_host(const nbldpc_code* cc, const uint8_t* gamma_host, int fra
   nbldpc_code* c = const_cast<nbldpc_code*>(cc);
   if (!c || frames < 0 || max_iters < 0 || chunk_frames <= 0) return NBLDPC_ERR_ARG;
   if (frames == 0) return NBLDPC_OK;
+  const int st = check_device(c);
+  if (st != NBLDPC_OK) return st;
   const size_t per = host_chunk_bytes(c, chunk_frames, (size_t)c->n * c->q, decode_ws_bytes(c, chunk_frames));
   return host_chunks(c, gamma_host, (size_t)c->n * c->q, frames, out_sym_host, out_iters_host, out_ok_host,
                      chunk_frames, workspace_dev, workspace_bytes, per, cuda_stream,

@@ -135,3 +135,31 @@ def test_header_and_library_from_plain_c(lib, tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr
     assert "c99 abi ok" in out.stdout
+
+
+def _function_body(src: str, name: str) -> str:
+    m = re.search(r"\b" + name + r"\([^;{]*\)\s*\{", src)
+    assert m, name
+    depth, i = 1, m.end()
+    while depth:
+        depth += {"{": 1, "}": -1}.get(src[i], 0)
+        i += 1
+    return src[m.end():i]
+
+
+def test_every_launching_entry_point_checks_the_device():
+    """A handle's code description lives in the memory of the device it was created on: every entry
+    point that queues GPU work on a handle compares the current device with it (check_device, which
+    returns NBLDPC_ERR_ARG otherwise) before it queues anything.  One GPU per box here, so this is a
+    check of the source: the check precedes the first launch or copy in each body."""
+    csrc = os.path.join(ROOT, "paper_2508_03567_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("nbldpc.cu", "fftspa_host.cu"))
+    for name in ("nbldpc_decode", "nbldpc_decode_noalloc", "nbldpc_decode_host", "nbldpc_code_autotune",
+                 "nbldpc_code_set_tuning", "nbldpc_code_set_message_bits", "nbldpc_code_set_cnp_schedule",
+                 "nbldpc_fftspa_decode", "nbldpc_fftspa_decode_host", "batch_plan"):
+        body = _function_body(src, name)
+        assert "check_device(c)" in body, name
+        first_work = min([body.find(w) for w in ("launch(", "launch_plan(", "fft_launch(", "host_chunks(",
+                                                 "configure(", "cudaMemsetAsync(") if w in body] or [len(body)])
+        assert body.find("check_device(c)") < first_work, name
+    assert "batch_plan(jobs, n_jobs" in _function_body(src, "nbldpc_decode_batch")
