@@ -57,6 +57,9 @@ def lib():
             L.orc_decode_cap.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                          i32p, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, u8p, i32p, u8p]
+            L.orc_decode_trace.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
+                                           i32p, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int,
+                                           i32p, i32p, i32p, u8p]
             L.orc_syndrome_ok.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                           i32p, i32p, i32p, u8p, ctypes.c_int, u8p]
             f32p = ctypes.POINTER(ctypes.c_float)
@@ -156,6 +159,26 @@ def decode(code, gamma: np.ndarray, max_iters: int, early_stop: int, threads: in
     if rc:
         raise ValueError("oracle rejected the code or arguments")
     return sym, its, ok
+
+
+def decode_trace(code, gamma: np.ndarray, iters: int, cap: int = 255):
+    """One frame (gamma [N, q]) decoded for exactly `iters` iterations without early stop:
+    (beta [E, q], S [N, q], alpha [E, q], symbols [N]) of the last iteration, edges in CSR order."""
+    g = np.ascontiguousarray(gamma, np.uint8)
+    assert g.shape == (code.n, code.q)
+    rp, ci, cf = _code_arrays(code)
+    e = int(rp[-1])
+    beta = np.zeros((e, code.q), np.int32)
+    s = np.zeros((code.n, code.q), np.int32)
+    alpha = np.zeros((e, code.q), np.int32)
+    sym = np.zeros(code.n, np.uint8)
+    rc = lib().orc_decode_trace(code.q, code.poly, code.n, code.m, _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32),
+                                _p(cf, ctypes.c_int32), _p(g, ctypes.c_uint8), int(iters), int(cap),
+                                _p(beta, ctypes.c_int32), _p(s, ctypes.c_int32), _p(alpha, ctypes.c_int32),
+                                _p(sym, ctypes.c_uint8))
+    if rc:
+        raise ValueError("oracle rejected the code or arguments")
+    return beta, s, alpha, sym
 
 
 def syndrome_ok(code, words: np.ndarray) -> np.ndarray:

@@ -160,9 +160,16 @@ int orc_check_update(int q, unsigned poly, int d, const int32_t *h, const uint8_
  * messages of the main reading; 65535 for the 16-bit-message comparison).
  * Returns 0, or -1 on invalid arguments (nothing written).
  */
-int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
-                   const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
-                   int cap, uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok) {
+/* Messages of the last iteration run, for tests (orc_decode_trace). */
+typedef struct {
+  int32_t *beta;   /* [E][q] check-node outputs */
+  int32_t *s;      /* [n][q] a-posteriori sums */
+  int32_t *alpha;  /* [E][q] variable-node outputs */
+} trace_t;
+
+static int decode_frames(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
+                         const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
+                         int cap, uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok, const trace_t *tr) {
   gf_t g;
   if (gf_build(&g, q, poly) || frames < 0 || max_iters < 0 || cap < 1) return -1;
   if (check_code(q, n, m, row_ptr, col_idx, coef)) return -1;
@@ -221,6 +228,8 @@ int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, c
           }
           cnp_one_check(&g, d, hrow, ap, bp, F, B, NULL);
         }
+        if (tr && k == max_iters)
+          for (size_t i = 0; i < (size_t)E * q; i++) tr->beta[i] = beta[i];
         /* VNP for every variable node:
          *   alpha'_{m,n}(x) = gamma_n(x) + sum over i in S_c(n)\m of beta_{i,n}(x)
          *   alpha_{m,n}(x)  = alpha'(x) - min_x alpha'(x), saturated at cap   */
@@ -245,12 +254,15 @@ int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, c
             int s = gam[(size_t)c * q + x];
             for (int b = vptr[c]; b < vptr[c + 1]; b++) s += beta[(size_t)vedge[b] * q + x];
             ap_sum[x] = s;
+            if (tr && k == max_iters) tr->s[(size_t)c * q + x] = s;
           }
           int best = 0;
           for (int x = 1; x < q; x++)
             if (ap_sum[x] < ap_sum[best]) best = x;
           chat[c] = best;
         }
+        if (tr && k == max_iters)
+          for (size_t i = 0; i < (size_t)E * q; i++) tr->alpha[i] = alpha[i];
         iters = k;
         ok = syndrome_ok(&g, m, row_ptr, col_idx, coef, chat);
         if (early_stop && ok) break;
@@ -263,6 +275,31 @@ int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, c
   free(vdeg); free(vptr); free(vfill); free(vedge); free(alpha); free(beta);
   free(F); free(B); free(ap); free(bp); free(hrow); free(chat); free(ap_sum);
   return 0;
+}
+
+int orc_decode_cap(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
+                   const int32_t *coef, const uint8_t *gamma, int frames, int max_iters, int early_stop,
+                   int cap, uint8_t *out_sym, int32_t *out_iters, uint8_t *out_ok) {
+  return decode_frames(q, poly, n, m, row_ptr, col_idx, coef, gamma, frames, max_iters, early_stop, cap, out_sym,
+                       out_iters, out_ok, NULL);
+}
+
+/*
+ * One frame decoded for exactly `iters` >= 1 iterations without early stop,
+ * returning, besides the decision, the messages of the last iteration: the
+ * check-node outputs beta [E][q], the a-posteriori sums S [n][q] of the
+ * decision and the variable-node outputs alpha [E][q] (edges in CSR order).
+ * The same loop as orc_decode_cap, which it shares; only the copies out are
+ * added.  Test helper for hand-worked iterations.
+ */
+int orc_decode_trace(int q, unsigned poly, int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
+                     const int32_t *coef, const uint8_t *gamma, int iters, int cap, int32_t *beta_out,
+                     int32_t *s_out, int32_t *alpha_out, uint8_t *out_sym) {
+  if (iters < 1) return -1;
+  trace_t tr = {beta_out, s_out, alpha_out};
+  int32_t its = 0;
+  uint8_t ok = 0;
+  return decode_frames(q, poly, n, m, row_ptr, col_idx, coef, gamma, 1, iters, 0, cap, out_sym, &its, &ok, &tr);
 }
 
 /* The main reading: 8-bit messages, saturation at 255. */

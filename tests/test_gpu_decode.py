@@ -433,3 +433,24 @@ def test_table1_schedule_limits():
     with pytest.raises(binding.NbldpcError) as ei:
         binding.nbldpc_code_set_cnp_schedule(dec.handle, binding.NBLDPC_CNP_TABLE1)
     assert ei.value.status == binding.NBLDPC_ERR_UNSUPPORTED
+
+
+# --------------------------------------------------------------- the hand-worked GF(4) iteration
+def test_eq1_worked_iteration_on_the_gpu():
+    """The Eq. (1) code and channel values of tests/golden/eq1_gf4_iteration1.txt: the decision after
+    1..3 iterations (every layout variant and frames-per-block count) equals the oracle's, and the
+    hand-derived decision of iteration 1 with the stop test after it."""
+    from test_oracle_pins import load_eq1, load_iteration1
+    g = load_iteration1()
+    code = I.code_from_dense(load_eq1(), 4, 0x7)
+    gamma = np.repeat(g["gamma"].astype(np.uint8)[None], 40, 0)
+    dec = binding.Decoder.from_code(code)
+    gt = torch.as_tensor(gamma).cuda()
+    for v in (0, 1):
+        for fpb in (1, 2, 4, 8):
+            dec.set_tuning(v, fpb)
+            for iters in (1, 2, 3):
+                got = [t.cpu().numpy() for t in dec.decode(gt, iters, 0)]
+                assert_same(got, oracle.decode(code, gamma, iters, 0), f"v{v} fpb{fpb} {iters} it")
+            s, i, o = (t.cpu().numpy() for t in dec.decode(gt, 5, 1))
+            assert np.all(s == g["decision"][0]) and np.all(i == 1) and np.all(o == 1)

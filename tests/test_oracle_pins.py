@@ -288,6 +288,70 @@ def test_eq1_code_decodes_a_single_symbol_error(oracle_lib):
     assert ok[0] == 1 and np.array_equal(sym[0], cw) and its[0] >= 1
 
 
+# ---------------------------------------------------------------- P9 one iteration by hand
+def load_iteration1():
+    """Sections of tests/golden/eq1_gf4_iteration1.txt as integer arrays."""
+    sec, cur = {}, None
+    with open(os.path.join(HERE, "golden", "eq1_gf4_iteration1.txt")) as fh:
+        for line in fh:
+            t = line.split("#")[0].strip()
+            if not t:
+                continue
+            if t.startswith("["):
+                cur = t.strip("[]")
+                sec[cur] = []
+                continue
+            sec[cur].append([int(v) for v in t.split(":")[-1].split()])
+    return {k: np.array(v, dtype=np.int64) for k, v in sec.items()}
+
+
+def test_eq1_one_iteration_worked_by_hand(oracle_lib):
+    """Alg. 2 at q = 4: one check-node pass and one variable-node pass on the Eq. (1) code, every
+    message compared with the values derived by hand in the golden file."""
+    g = load_iteration1()
+    code = I.code_from_dense(load_eq1(), 4, 0x7)
+    gamma = g["gamma"].astype(np.uint8)
+    assert gamma.shape == (6, 4) and g["beta"].shape == g["alpha"].shape == (code.nnz, 4)
+    for r in range(code.m):             # the check-node pass alone, row by row, from alpha^(0) = gamma
+        e = slice(code.row_ptr[r], code.row_ptr[r + 1])
+        beta = oracle_lib.check_update(4, 0x7, code.coef[e], gamma[code.col_idx[e]])
+        assert np.array_equal(beta, g["beta"][e]), r
+    beta, s, alpha, sym = oracle_lib.decode_trace(code, gamma, 1)
+    assert np.array_equal(beta, g["beta"])
+    assert np.array_equal(s, g["S"])
+    assert np.array_equal(alpha, g["alpha"])
+    assert np.array_equal(sym, g["decision"][0])
+    # the stop test: the channel decision fails check 0, the decision of iteration 1 is a codeword
+    sym0, its0, ok0 = oracle_lib.decode(code, gamma[None], 0, 1)
+    assert sym0[0].tolist() == [0, 0, 0, 1, 0, 0] and its0[0] == 0 and ok0[0] == 0
+    sym1, its1, ok1 = oracle_lib.decode(code, gamma[None], 5, 1)
+    assert np.array_equal(sym1[0], g["decision"][0]) and its1[0] == 1 and ok1[0] == 1
+
+
+def test_eq1_worked_iteration_tells_the_planted_mistakes_apart():
+    """The hand-worked case separates the readings a plausible mistake would change: for some edges
+    the variable-node sum gamma + (other beta) is smallest at a non-zero symbol, so normalizing by
+    its value at symbol 0 would give other messages; and column 3's a-posteriori sum ties at its
+    minimum, so the highest-symbol tie-break would decide 1 there, which fails check 0."""
+    g = load_iteration1()
+    code = I.code_from_dense(load_eq1(), 4, 0x7)
+    gamma, beta, alpha = g["gamma"], g["beta"], g["alpha"]
+    shifted = 0
+    for n in range(code.n):
+        edges = np.nonzero(code.col_idx == n)[0]
+        assert len(edges) == 2
+        for e, other in ((edges[0], edges[1]), (edges[1], edges[0])):
+            a_prime = gamma[n] + beta[other]
+            assert np.array_equal(alpha[e], a_prime - a_prime.min())
+            shifted += int(a_prime[0] != a_prime.min())
+    assert shifted >= 3
+    s3 = g["S"][3]
+    assert (s3 == s3.min()).sum() == 2 and g["decision"][0][3] == 0
+    word = g["decision"][0].copy()
+    word[3] = int(np.nonzero(s3 == s3.min())[0].max())
+    assert not syndrome_indep(code, word[None].astype(np.uint8))[0]
+
+
 # ---------------------------------------------------------------- input generator
 def test_inputs_are_codewords_and_reliabilities(oracle_lib):
     for name in ["gf4_n48_dv2_dc4", "gf64_n576_dv2_dc4", "gf32_n600_dv3_dc6"]:
