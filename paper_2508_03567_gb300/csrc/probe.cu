@@ -6,7 +6,8 @@
 //
 // Register forms: every thread repeats the shuffle step of the convolution's
 // inner loop on registers -- 8 accumulators, 4 packed A words, 8 packed B
-// words, 32 maxima and 32 minima per step, 4 steps per round -- with a chosen
+// words per step (32 in all), 32 maxima and 32 minima per step, 4 steps per
+// round -- with a chosen
 // share of the maxima computed on the FMA pipe (vmax2_fma) and, optionally,
 // the A words of steps 1..3 fetched by shfl.xor as in mm_conv.  Each round
 // feeds its accumulators back as the next round's A words, so nothing can be
@@ -30,14 +31,18 @@ constexpr int kProbeThreads = 256;
 
 // FMA32: how many of the 32 maxima of a step use the FMA pipe; SHFL: A words
 // of steps 1..3 come from lane offsets 2, 4, 6 (the convolution's exchange).
+// Every step has its own 8 B words (32 registers, as the convolution holds
+// them), so the 128 maxima of a round are 128 distinct pairs.
 template <int FMA32, bool SHFL>
 __global__ void __launch_bounds__(kProbeThreads) probe_mix_kernel(int rounds, unsigned int* sink) {
-  uint32_t a[4], b[8], acc[8];
+  uint32_t a[4], b[4][8], acc[8];
   const uint32_t t0 = threadIdx.x * 0x00010001u;
 #pragma unroll
   for (int i = 0; i < 4; ++i) a[i] = (t0 + 0x00050003u * (i + 1)) & 0x00FF00FFu;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) b[i] = (t0 * 7u + 0x000B0011u * (i + 3)) & 0x00FF00FFu;
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[s][i] = (t0 * 7u + 0x000B0011u * (8 * s + i + 3)) & 0x00FF00FFu;
 #pragma unroll
   for (int i = 0; i < 8; ++i) acc[i] = 0x00FF00FFu;
   for (int k = 0; k < rounds; ++k) {
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_mix_kernel(int rounds, un
       for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const uint32_t m = (r * 4 + t < FMA32) ? vmax2_fma(av[t], b[r ^ t]) : vmax2(av[t], b[r ^ t]);
+          const uint32_t m = (r * 4 + t < FMA32) ? vmax2_fma(av[t], b[s][r ^ t]) : vmax2(av[t], b[s][r ^ t]);
           acc[r] = vmin2(acc[r], m);
         }
     }
