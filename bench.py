@@ -378,101 +378,119 @@ def run_peak(args, ws, rank, local):
 
 
 # ---------------------------------------------------------------- one min-max workload
-def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, frames=None, graph_repeat=0,
+L2_BYTES = 129e6
+
+
+def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, frames=None, graph=False,
                      cpu_frames=None, e2e=True, profile=None):
     """One min-max workload of inputs.WORKLOADS through nbldpc_decode: its frames
     at every Eb/N0 point (inputs resident in HBM), `warmup` untimed and `steps`
     timed decodes (CUDA events on the launching stream), info Mbit/s, frame
     error rate against the transmitted codewords, the ALU roofline, clocks,
-    and optionally a CUDA-graph replay of `graph_repeat` decodes, the e2e
-    host-buffer decode and the CPU oracle on a sample."""
+    and optionally a CUDA-graph replay, the e2e host-buffer decode and the CPU
+    oracle on a sample.  A step whose inputs are smaller than L2 is one batch
+    of a pool of distinct batches, 2 x L2 in all, decoded in turn, so that no
+    timed decode finds its inputs in L2; the graph then holds one decode per
+    batch of the pool."""
     w = I.WORKLOADS[name]
     code = I.workload_code(name)
     fpp = frames or w["frames"]
+    npts = len(w["ebn0"])
+    step_bytes = npts * fpp * code.n * code.q
+    pool = 1 if step_bytes > L2_BYTES else int(np.ceil(2 * L2_BYTES / step_bytes))
     gam, cws = [], []
     for i, eb in enumerate(w["ebn0"]):
-        b = I.make_batch(code, eb, I.workload_seed(name, i), fpp, device=dev, chunk=8192)
-        gam.append(b.gamma)
-        cws.append(b.codewords)
-    gamma = torch.cat(gam, 0).contiguous()
-    cw = torch.cat(cws, 0)
+        bt = I.make_batch(code, eb, I.workload_seed(name, i), pool * fpp, device=dev, chunk=65536)
+        gam.append(bt.gamma.view(pool, fpp, code.n, code.q))
+        cws.append(bt.codewords.view(pool, fpp, code.n))
+    gamma = torch.cat(gam, 1).contiguous()                 # [pool, frames per step, n, q]
+    cw = torch.cat(cws, 1)
     del gam, cws
-    nf = gamma.shape[0]
+    nf = gamma.shape[1]
     dec = binding.Decoder.from_code(code)
     tuning = {"source": "default"}
     if not args.no_autotune:
-        res = dec.autotune(gamma[: min(nf, 4096)], 3)
+        res = dec.autotune(gamma[0][: min(nf, 4096)], 3)
         tuning = {"source": "autotuned", "candidates_ms": {f"v{v}_fpb{f}": round(ms, 3) for v, f, ms in res}}
     v, fpb = dec.tuning()
     tuning.update({"variant": v, "frames_per_block": fpb})
     stream = torch.cuda.Stream(device=dev)
-    sym = torch.empty((nf, code.n), dtype=torch.uint8, device=dev)
-    its = torch.empty((nf,), dtype=torch.int32, device=dev)
-    ok = torch.empty((nf,), dtype=torch.uint8, device=dev)
+    sym = torch.empty((pool, nf, code.n), dtype=torch.uint8, device=dev)
+    its = torch.empty((pool, nf), dtype=torch.int32, device=dev)
+    ok = torch.empty((pool, nf), dtype=torch.uint8, device=dev)
     wsb = dec.workspace(nf, dev)
     mi, es = w["max_iters"], w["early_stop"]
 
-    def step():
-        binding.nbldpc_decode(dec.handle, gamma, nf, mi, es, sym, its, ok, wsb, stream=stream)
+    def step(i):
+        b = i % pool
+        binding.nbldpc_decode(dec.handle, gamma[b], nf, mi, es, sym[b], its[b], ok[b], wsb, stream=stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            step()
+        for i in range(warmup):
+            step(i)
+        for i in range(warmup, pool):      # every batch of the pool decoded once (outputs for the FER)
+            step(i)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ksteps = max(steps, min(pool, 1000))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ksteps)]
     launches0 = binding.nbldpc_kernel_launch_count()
     with ClockSampler(local) as clk:
-        for a, b in ev:
+        for i, (a, b) in enumerate(ev):
             a.record(stream)
-            step()
+            step(warmup + i)
             b.record(stream)
         torch.cuda.synchronize()
     launches = binding.nbldpc_kernel_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kernel_s = statistics.mean(step_ms) / 1e3
     its_h = its.cpu().numpy().astype(np.int64)
-    pairs_step = int(its_h.sum()) * pairs_per_frame_iter(code)
+    pairs_step = int(its_h.sum()) * pairs_per_frame_iter(code) / pool
     achieved = 2 * pairs_step / kernel_s / 1e9
     peak, kind, issue = peaks
     bpf = profiled_traffic(profile)[0] if profile else None
     info_bits = nf * code.k * code.p
-    out = {"workload": name, "value": info_bits / kernel_s / 1e6, "unit": "Mbit/s", "steps": steps,
+    out = {"workload": name, "value": info_bits / kernel_s / 1e6, "unit": "Mbit/s", "steps": ksteps,
            "warmup": warmup, "ms_per_step": 1e3 * kernel_s, "median_ms_per_step": statistics.median(step_ms),
            "config": {"q": code.q, "n": code.n, "k": code.k, "dv": w["dv"], "dc": w["dc"], "frames_per_step": nf,
                       "ebn0_db": list(w["ebn0"]), "max_iters": mi, "early_stop": bool(es), "tuning": tuning,
-                      "l2": "inputs larger than L2 (no flush)" if gamma.numel() > 129e6 else
-                            "inputs smaller than L2: resident across steps"},
+                      "l2": "inputs larger than L2 (no flush)" if pool == 1 else
+                            f"each step decodes the next of {pool} distinct {nf}-frame batches "
+                            f"({pool * step_bytes / 1e6:.0f} MB of inputs, > L2; no flush)"},
            "roofline": roofline_alu(achieved, peak, kind, issue, None if bpf is None else bpf * nf),
            "clocks": clk.summary(), "gpu_launches": int(launches),
-           "fer": float((sym.to(torch.int64) != cw).any(1).float().mean()),
+           "fer": float((sym.to(torch.int64) != cw).any(-1).float().mean()),
            "not_ok": float(1 - ok.float().mean()), "mean_iters": float(its_h.mean()),
            "pairs_per_step": pairs_step, "coded_mbps": info_bits / kernel_s / 1e6 * code.n / code.k}
-    if graph_repeat:
-        # the same decode captured `graph_repeat` times in one CUDA graph: launch cost off the host
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=stream):
-            for _ in range(graph_repeat):
-                step()
+    if graph:
+        # one decode per batch of the pool (or `steps` decodes of the one batch) captured in a CUDA graph
+        reps = pool if pool > 1 else steps
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for i in range(reps):
+                step(i)
+
         def replay():
             with torch.cuda.stream(stream):
-                graph.replay()
-        for _ in range(2):
-            replay()
+                g.replay()
+        replay()
         torch.cuda.synchronize()
-        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in gev:
-            a.record(stream)
-            replay()
-            b.record(stream)
-        torch.cuda.synchronize()
-        per = sum(a.elapsed_time(b) for a, b in gev) / (steps * graph_repeat) / 1e3
-        gp = int(its.cpu().numpy().astype(np.int64).sum()) * pairs_per_frame_iter(code)
+        nrep = 5
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nrep)]
+        with ClockSampler(local) as gclk:
+            for a, b in gev:
+                a.record(stream)
+                replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+        per = sum(a.elapsed_time(b) for a, b in gev) / (nrep * reps) / 1e3
         out["graph"] = {"value": info_bits / per / 1e6, "unit": "Mbit/s", "ms_per_decode": 1e3 * per,
-                        "decodes_per_replay": graph_repeat, "replays": steps,
-                        "roofline": roofline_alu(2 * gp / per / 1e9, peak, kind, issue),
-                        "form": f"{graph_repeat} nbldpc_decode calls captured in one CUDA graph, replayed"}
+                        "decodes_per_replay": reps, "replays": nrep, "clocks": gclk.summary(),
+                        "roofline": roofline_alu(2 * pairs_step / per / 1e9, peak, kind, issue),
+                        "form": f"{reps} nbldpc_decode calls captured in one CUDA graph, replayed"}
+        if not out["clocks"]:
+            out["clocks"] = gclk.summary()
     if e2e and not args.no_e2e:
-        out["e2e"] = measure_e2e(binding, dec, code, gamma, mi, es, args, dev)
+        out["e2e"] = measure_e2e(binding, dec, code, gamma[0], mi, es, args, dev)
     if cpu_frames and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(name, *cpu_frames)
     del gamma
@@ -1012,7 +1030,7 @@ def make_inputs_cw(code, w, frames_per_point, device, rank):
     return torch.cat(gam, 0).contiguous(), torch.cat(cws, 0)
 
 
-def run_single(args, ws, rank, local, name, graph_repeat=0, cpu_frames=None, profile=None):
+def run_single(args, ws, rank, local, name, graph=False, cpu_frames=None, profile=None):
     """--workload gf4 / gf256: one min-max workload as its own line."""
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -1025,7 +1043,7 @@ def run_single(args, ws, rank, local, name, graph_repeat=0, cpu_frames=None, pro
     torch.cuda.set_device(dev)
     peaks = alu_peaks(None if args.no_extras else measure_peak(binding, dev, local, 0.3, PROBE_FORMS), dev)
     r = measure_workload(binding, I, name, dev, local, args, peaks, args.steps, args.warmup,
-                         frames=args.frames, graph_repeat=graph_repeat, cpu_frames=cpu_frames, profile=profile)
+                         frames=args.frames, graph=graph, cpu_frames=cpu_frames, profile=profile)
     line = {"metric": "decoded info Mbit/s", "value": r.pop("value"), "unit": "Mbit/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -1034,10 +1052,10 @@ def run_single(args, ws, rank, local, name, graph_repeat=0, cpu_frames=None, pro
     return 0
 
 
-# workloads beside the headline: (name, graph-replay repeat, CPU sample (all cores, one thread) per Eb/N0
+# workloads beside the headline: (name, CUDA-graph replay, CPU sample (all cores, one thread) per Eb/N0
 # point, committed ncu summary)
-SIDE_WORKLOADS = (("gf4_n48_dv2_dc4", 100, (1000, 1000), "mma_decode_kernel_gf4_n48.md"),
-                  ("gf256_n384_dv2_dc6", 0, (16, 2), "mma_decode_kernel_gf256_n384.md"))
+SIDE_WORKLOADS = (("gf4_n48_dv2_dc4", True, (1000, 1000), "mma_decode_kernel_gf4_n48.md"),
+                  ("gf256_n384_dv2_dc6", False, (16, 2), "mma_decode_kernel_gf256_n384.md"))
 
 
 def main():
@@ -1148,7 +1166,7 @@ def main():
         ks, kw = min(args.steps, 5), 3
         side = {}
         for name, rep, cpuf, prof in SIDE_WORKLOADS:
-            side[name] = measure_workload(binding, I, name, dev, local, args, peaks, ks, kw, graph_repeat=rep,
+            side[name] = measure_workload(binding, I, name, dev, local, args, peaks, ks, kw, graph=rep,
                                           cpu_frames=cpuf, profile=prof)
             torch.cuda.empty_cache()
         # GF(4) N=48 at a batch large enough that launch cost does not dominate (kernel rate)
