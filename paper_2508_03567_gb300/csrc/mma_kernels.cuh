@@ -50,9 +50,10 @@ __device__ __forceinline__ uint32_t vmax2_fma(uint32_t a, uint32_t b) {
 // Bytes of one variable node's q-byte rows that each lane of the variable-node
 // pass handles (q / VBPL lanes per node).  Wide lanes put several nodes in
 // flight per warp and shorten the shuffle reductions; measured on GB300 the
-// 4-byte lanes of GF(64) left that pass latency-bound (8 bytes: +10 %).
+// 4-byte lanes of GF(64) left that pass latency-bound (8 bytes: +10 %, 16
+// bytes: +3 % more).
 #ifndef NBLDPC_VBPL_64
-#define NBLDPC_VBPL_64 8
+#define NBLDPC_VBPL_64 16
 #endif
 #ifndef NBLDPC_VBPL_256
 #define NBLDPC_VBPL_256 16
@@ -87,6 +88,13 @@ template <> struct Layout<256, 1> { static constexpr int LB = 4, SB = 1; };
 
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
+// bytes of one 16-bit message vector in shared memory (NBLDPC_VPAD: padding
+// that shifts consecutive vectors to other banks)
+#ifndef NBLDPC_VPAD
+#define NBLDPC_VPAD 0
+#endif
+template <int Q> __host__ __device__ constexpr int vec_bytes() { return (2 * Q + 15) / 16 * 16 + NBLDPC_VPAD; }
+
 template <int Q_, int V_> struct Geo {
   static constexpr int Q = Q_, V = V_;
   static constexpr int P = ilog2(Q);
@@ -103,7 +111,7 @@ template <int Q_, int V_> struct Geo {
   static constexpr int W = Q / 2;               // 32-bit words per vector
   static constexpr int PW = (W + G - 1) / G;    // permutation words per lane
   static constexpr int BPL = Q / G;             // bytes per lane when a group writes q bytes
-  static constexpr int VB = (2 * Q + 15) / 16 * 16;  // bytes per 16-bit vector in smem
+  static constexpr int VB = vec_bytes<Q>();     // bytes per 16-bit vector in smem
   // variable-node pass: VG lanes per variable node, VBPL bytes (VBPL/2 packed words) each
   static constexpr int VBPL = VnpBytes<Q>::v;
   static constexpr int VG = Q / VBPL;
@@ -255,12 +263,22 @@ struct LaunchParams {
   int blob_cap, n_cap;        // largest code blob and N among the jobs
 };
 
-template <int Q> __host__ __device__ constexpr int vec_bytes() { return (2 * Q + 15) / 16 * 16; }
 
-// per-group shared scratch: the d incoming rows (q symbols of mb bytes each)
-// and 2*dmax+3 16-bit vectors
+// Check-node permutation by scatter from registers (8-bit messages, 16 <= q <=
+// NBLDPC_SCATTER_MAXQ) instead of staging the incoming rows in shared memory
+// and gathering them.
+#ifndef NBLDPC_SCATTER_MAXQ
+#define NBLDPC_SCATTER_MAXQ 256
+#endif
+template <int Q> __host__ __device__ constexpr bool scatter_perm(int mb) {
+  return mb == 1 && Q >= 16 && Q <= NBLDPC_SCATTER_MAXQ;
+}
+
+// per-group shared scratch: the d incoming rows (q symbols of mb bytes each;
+// not with the scatter permutation) and 2*dmax+1 16-bit vectors: P_0..P_{d-1},
+// F_1..F_{d-2}, two B vectors and the middle beta R
 template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax, int mb = 1) {
-  return ((dmax * Q * mb + 15) / 16) * 16 + (2 * dmax + 3) * vec_bytes<Q>();
+  return (scatter_perm<Q>(mb) ? 0 : ((dmax * Q * mb + 15) / 16) * 16) + (2 * dmax + 1) * vec_bytes<Q>();
 }
 
 // named barrier over the threads of one frame slot (ids 1..fpb)
@@ -349,6 +367,7 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // ---------------------------------------------------------------- one frame
+
 // Decodes frame `frame` of `job` with the nthr threads of one frame slot
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
@@ -359,6 +378,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   constexpr int Q = g::Q;
   constexpr int PW = g::PW;
   constexpr int RS = Q * MB;                 // bytes of one message row
+  constexpr bool kScatter = scatter_perm<Q>(MB);
   static_assert(MB == 1 || MB == 2, "message bytes");
   const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
   const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
@@ -379,39 +399,32 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   const int vgrp = stid / g::VG, nvgroups = nthr / g::VG;
   const int vgl = stid % g::VG;
   const unsigned vmask = group_mask<g::VG>(lane);
-  // symbol values of this lane's packed words in the variable-node pass
-  uint32_t vsym[g::VW];
-#pragma unroll
-  for (int i = 0; i < g::VW; ++i)
-    vsym[i] = (uint32_t)(vgl * g::VBPL + 2 * i) | ((uint32_t)(vgl * g::VBPL + 2 * i + 1) << 16);
 
-  // lane constants for the coefficient permutations: logarithms of the
-  // symbols this lane gathers (permutation) and writes (de-permutation),
-  // packed 8 bits per symbol; the zero symbol, which every multiplication
-  // fixes, is flagged separately.
+  // lane constants for the gather permutation (staged rows): logarithms of the
+  // symbols this lane gathers, packed 8 bits per symbol; the zero symbol, which
+  // every multiplication fixes, is flagged separately.
   uint32_t py_log0 = 0, py_log1 = 0, py_nz0 = 0;   // word i: bits [8i, 8i+8)
+  if constexpr (!kScatter) {
 #pragma unroll
-  for (int i = 0; i < PW; ++i) {
-    const int w = gl + i * g::G;
-    if (w < g::W) {
-      if (w) { py_log0 |= (uint32_t)glog[2 * w] << (8 * i); py_nz0 |= 1u << i; }
-      py_log1 |= (uint32_t)glog[2 * w + 1] << (8 * i);
+    for (int i = 0; i < PW; ++i) {
+      const int w = gl + i * g::G;
+      if (w < g::W) {
+        if (w) { py_log0 |= (uint32_t)glog[2 * w] << (8 * i); py_nz0 |= 1u << i; }
+        py_log1 |= (uint32_t)glog[2 * w + 1] << (8 * i);
+      }
     }
   }
-  uint64_t da_log = 0;
-  uint32_t da_mask = 0;
-#pragma unroll
-  for (int i = 0; i < g::BPL; ++i) {
-    const int a = gl * g::BPL + i;
-    if (a) { da_log |= (uint64_t)glog[a] << (8 * i); da_mask |= 1u << i; }
-  }
+  // de-permutation: log of the first symbol this lane writes (-1 for symbol 0)
+  const int da_log0 = gl ? (int)glog[gl * g::BPL] : -1;
 
   unsigned char* gs = scratch + (size_t)grp * job.group_bytes;
-  uint8_t* stage = gs;                                                   // [dmax][q * MB] bytes
-  unsigned char* vecs = gs + ((job.dmax * RS + 15) / 16) * 16;
+  uint8_t* stage = gs;                                                   // [dmax][q * MB] bytes (staged rows)
+  unsigned char* vecs = gs + (kScatter ? 0 : ((job.dmax * RS + 15) / 16) * 16);
   auto vec = [&](int i) { return reinterpret_cast<uint32_t*>(vecs + (size_t)i * g::VB); };
   auto vec16 = [&](int i) { return reinterpret_cast<uint16_t*>(vecs + (size_t)i * g::VB); };
-  // vectors: P_j = vec(j), F_j = vec(dmax + j), B ping-pong = vec(2dmax), vec(2dmax+1), R = vec(2dmax+2)
+  // vectors: P_j = vec(j) (j < dmax), F_j = vec(dmax + j - 1) (1 <= j <= d-2),
+  // B ping-pong = vec(2 dmax - 2), vec(2 dmax - 1), R = vec(2 dmax)
+  const int vF = job.dmax - 1, vB = 2 * job.dmax - 2, vR = 2 * job.dmax;
   const uint8_t* gam = job.gamma + (size_t)frame * job.n * Q;
 
     // ---- variable-node pass (Alg. 2, VNP and hard decision):
@@ -466,6 +479,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     };
 
     auto vnp = [&](bool first, bool want_alpha) {
+      // symbol values of this lane's packed words: (a, a + 1), a = vgl * VBPL + 2 i
+      const uint32_t vsym0 = (uint32_t)(vgl * g::VBPL) * 0x10001u + 0x10000u;
       for (int vn = vgrp; vn < job.n; vn += nvgroups) {
         uint32_t S[g::VW];
         load_pairs<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
@@ -480,9 +495,9 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         }
         int key;
         if (job.key16) {        // key = S * q + a fits 16 bits: minimum value, lowest symbol
-          uint32_t kw = S[0] * (uint32_t)Q + vsym[0];
+          uint32_t kw = S[0] * (uint32_t)Q + vsym0;
 #pragma unroll
-          for (int i = 1; i < g::VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + vsym[i]);
+          for (int i = 1; i < g::VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + (vsym0 + 0x20002u * i));
           key = (int)min(kw & 0xFFFFu, kw >> 16);
           key = group_min<g::VG>(key, vmask);
           if (vgl == 0) chat[vn] = (uint8_t)(key & (Q - 1));
@@ -490,8 +505,9 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
           key = 0x7FFFFFFF;
 #pragma unroll
           for (int i = 0; i < g::VW; ++i) {
-            key = min(key, (int)(((S[i] & 0xFFFFu) << 8) | (vsym[i] & 0xFFFFu)));
-            key = min(key, (int)(((S[i] >> 16) << 8) | (vsym[i] >> 16)));
+            const uint32_t sy = vsym0 + 0x20002u * i;
+            key = min(key, (int)(((S[i] & 0xFFFFu) << 8) | (sy & 0xFFFFu)));
+            key = min(key, (int)(((S[i] >> 16) << 8) | (sy >> 16)));
           }
           key = group_min<g::VG>(key, vmask);
           if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
@@ -517,7 +533,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       }
     };
 
-    // ---- syndrome of chat over all checks (block-wide)
+    // ---- syndrome of chat over all checks (slot-wide)
     auto syndrome_ok = [&]() -> bool {
       int bad = 0;
       for (int r = stid; r < job.m; r += nthr) {
@@ -532,60 +548,92 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     };
 
     // ---- check-node pass (Alg. 2, F & B matrices and beta), one group per check
+    constexpr int CH = Q / 16 > 0 ? Q / 16 : 1;          // 16-byte pieces of one 8-bit row
+    // scatter permutation: piece c of the check (edges e0 ..) holds symbols
+    // a = 16 part + k (k < 16) of edge j = c / CH, part = c % CH, and
+    // P_j(h_j a) = alpha_j(a) with h (16 part + k) = h (16 part) ^ h k, both
+    // XOR sums of the h x^b = exp2[log h + b]
+    auto scatter_piece = [&](bool first, int e0, int c) {
+      const int j = c / CH, part = c - j * CH;
+      const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
+      const uint4 v = reinterpret_cast<const uint4*>(src)[part];
+      const int lh = edge_lh[e0 + j];
+      const int h1 = exp2[lh], h2 = exp2[lh + 1], h4 = exp2[lh + 2], h8 = exp2[lh + 3];
+      int yb = 0;
+#pragma unroll
+      for (int b = 4; b < g::P; ++b)
+        if ((part >> (b - 4)) & 1) yb ^= exp2[lh + b];
+      uint16_t* Pv = vec16(j);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int y = yb ^ ((k & 1) ? h1 : 0) ^ ((k & 2) ? h2 : 0) ^ ((k & 4) ? h4 : 0) ^ ((k & 8) ? h8 : 0);
+        Pv[y] = (uint16_t)__byte_perm(w[k >> 2], 0, 0x4440 | (k & 3));
+      }
+    };
     auto cnp = [&](bool first) {
       for (int r = grp; r < job.m; r += ngroups) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
-        // stage incoming alpha rows (alpha^(0) = gamma on the first pass)
-        if constexpr (MB == 2) {
-          constexpr int CH = RS / 16 > 0 ? RS / 16 : 1, CB = RS / CH;   // chunks of CB bytes
-          for (int i = gl; i < d * CH; i += g::G) {
-            const int j = i / CH, c = i % CH;
-            const uint8_t* src = X + (size_t)(e0 + j) * RS + c * CB;
-            uint8_t* dst = stage + j * RS + c * CB;
-            if constexpr (CB == 16) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
-            else if constexpr (CB == 8) *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
-            else *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<const uint32_t*>(src);
-          }
-        } else if constexpr (Q >= 16) {
-          constexpr int CH = Q / 16;
-          for (int i = gl; i < d * CH; i += g::G) {
-            const int j = i / CH, c = i % CH;
-            const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
-            reinterpret_cast<uint4*>(stage + j * Q)[c] = reinterpret_cast<const uint4*>(src)[c];
-          }
+        if constexpr (kScatter) {
+          for (int c = gl; c < d * CH; c += g::G) scatter_piece(first, e0, c);
         } else {
-          for (int i = gl; i < d * Q; i += g::G) {
-            const int j = i / Q, c = i % Q;
-            const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
-            stage[i] = src[c];
+          // stage incoming alpha rows (alpha^(0) = gamma on the first pass)
+          if constexpr (MB == 2) {
+            constexpr int CH2 = RS / 16 > 0 ? RS / 16 : 1, CB = RS / CH2;   // chunks of CB bytes
+            for (int i = gl; i < d * CH2; i += g::G) {
+              const int j = i / CH2, c = i % CH2;
+              const uint8_t* src = X + (size_t)(e0 + j) * RS + c * CB;
+              uint8_t* dst = stage + j * RS + c * CB;
+              if constexpr (CB == 16) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+              else if constexpr (CB == 8) *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+              else *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<const uint32_t*>(src);
+            }
+          } else if constexpr (Q >= 16) {
+            for (int i = gl; i < d * CH; i += g::G) {
+              const int j = i / CH, c = i % CH;
+              const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
+              reinterpret_cast<uint4*>(stage + j * Q)[c] = reinterpret_cast<const uint4*>(src)[c];
+            }
+          } else {
+            for (int i = gl; i < d * Q; i += g::G) {
+              const int j = i / Q, c = i % Q;
+              const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
+              stage[i] = src[c];
+            }
           }
-        }
-        group_sync<g::G>(gmask);
-        // permutation: P_j(y) = alpha_j(h_j^-1 y), 16-bit natural order
-        for (int j = 0; j < d; ++j) {
-          const int lhinv = edge_lhi[e0 + j];
-          const uint8_t* a = stage + j * RS;
-          const uint16_t* a16 = reinterpret_cast<const uint16_t*>(a);
-          uint32_t* P = vec(j);
+          group_sync<g::G>(gmask);
+          // permutation: P_j(y) = alpha_j(h_j^-1 y), 16-bit natural order
+          for (int j = 0; j < d; ++j) {
+            const int lhinv = edge_lhi[e0 + j];
+            const uint8_t* a = stage + j * RS;
+            const uint16_t* a16 = reinterpret_cast<const uint16_t*>(a);
+            uint32_t* P = vec(j);
 #pragma unroll
-          for (int i = 0; i < PW; ++i) {
-            const int w = gl + i * g::G;
-            if (PW * g::G == g::W || w < g::W) {
-              const int s0 = (py_nz0 >> i) & 1 ? exp2[((py_log0 >> (8 * i)) & 0xFF) + lhinv] : 0;
-              const int s1 = exp2[((py_log1 >> (8 * i)) & 0xFF) + lhinv];
-              if constexpr (MB == 2) P[w] = (uint32_t)a16[s0] | ((uint32_t)a16[s1] << 16);
-              else P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
+            for (int i = 0; i < PW; ++i) {
+              const int w = gl + i * g::G;
+              if (PW * g::G == g::W || w < g::W) {
+                const int s0 = (py_nz0 >> i) & 1 ? exp2[((py_log0 >> (8 * i)) & 0xFF) + lhinv] : 0;
+                const int s1 = exp2[((py_log1 >> (8 * i)) & 0xFF) + lhinv];
+                if constexpr (MB == 2) P[w] = (uint32_t)a16[s0] | ((uint32_t)a16[s1] << 16);
+                else P[w] = (uint32_t)a[s0] | ((uint32_t)a[s1] << 16);
+              }
             }
           }
         }
         group_sync<g::G>(gmask);
-        // beta_j(a) = R_j(h_j a), written over the edge's message row
+        // beta_j(a) = R_j(h_j a), written over the edge's message row; the lane's
+        // symbols are a0 + i (a0 = gl * BPL, i < BPL) and h (a0 + i) = h a0 ^ h i
         auto depermute = [=](const uint16_t* R16, int e) {
           const int lh = edge_lh[e];
+          const int base = da_log0 >= 0 ? (int)exp2[da_log0 + lh] : 0;
+          int hb[3] = {0, 0, 0};
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            if ((1 << b) < g::BPL) hb[b] = exp2[lh + b];
           int out[g::BPL];
 #pragma unroll
           for (int i = 0; i < g::BPL; ++i)
-            out[i] = R16[(da_mask >> i) & 1 ? exp2[((da_log >> (8 * i)) & 0xFF) + lh] : 0];
+            out[i] = R16[base ^ ((i & 1) ? hb[0] : 0) ^ ((i & 2) ? hb[1] : 0) ^ ((i & 4) ? hb[2] : 0)];
           if constexpr (MB == 2) {
             uint16_t* row = reinterpret_cast<uint16_t*>(X + (size_t)e * RS) + gl * g::BPL;
 #pragma unroll
@@ -597,25 +645,24 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
         int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<g, MB == 1>(vec(fprev), vec(j), vec16(job.dmax + j), cl, gmask);
+          mm_conv<g, MB == 1>(vec(fprev), vec(j), vec16(vF + j), cl, gmask);
           group_sync<g::G>(gmask);
-          fprev = job.dmax + j;
+          fprev = vF + j;
         }
         depermute(vec16(fprev), e0 + d - 1);               // beta_{d-1} from F_{d-2}
         if constexpr (T1) {          // Table 1 schedule: F_{d-1} into the scratch vector, unused
-          mm_conv<g, MB == 1>(vec(fprev), vec(d - 1), vec16(2 * job.dmax + 2), cl, gmask);
+          mm_conv<g, MB == 1>(vec(fprev), vec(d - 1), vec16(vR), cl, gmask);
           group_sync<g::G>(gmask);
         }
         // backward: B_{d-1} = P_{d-1}; beta_j from F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j
         int bcur = d - 1;
         int pp = 0;
         for (int j = d - 2; j >= 1; --j) {
-          const int fj = (j == 1) ? 0 : job.dmax + j - 1;
-          const int rv = 2 * job.dmax + 2;
-          mm_conv<g, MB == 1>(vec(fj), vec(bcur), vec16(rv), cl, gmask);
+          const int fj = (j == 1) ? 0 : vF + j - 1;
+          mm_conv<g, MB == 1>(vec(fj), vec(bcur), vec16(vR), cl, gmask);
           group_sync<g::G>(gmask);
-          depermute(vec16(rv), e0 + j);
-          const int bn = 2 * job.dmax + pp;
+          depermute(vec16(vR), e0 + j);
+          const int bn = vB + pp;
           mm_conv<g, MB == 1>(vec(bcur), vec(j), vec16(bn), cl, gmask);
           group_sync<g::G>(gmask);
           bcur = bn;
@@ -623,17 +670,19 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         }
         depermute(vec16(bcur), e0);                        // beta_0 from B_1
         if constexpr (T1)            // Table 1 schedule: B_0 into the scratch vector, unused
-          mm_conv<g, MB == 1>(vec(bcur), vec(0), vec16(2 * job.dmax + 2), cl, gmask);
+          mm_conv<g, MB == 1>(vec(bcur), vec(0), vec16(vR), cl, gmask);
         group_sync<g::G>(gmask);
       }
     };
 
-    // ---- decode one frame
+    // ---- decode one frame.  Without early stop only the final decision is
+    // tested, so the stop test runs once, after the last iteration.
+    const bool es = job.early_stop != 0;
     if constexpr (MB == 2) vnp_wide(true, false); else vnp(true, false);   // c^(0) = argmin gamma
     slot_sync(bar_id, nthr);
-    bool ok = syndrome_ok();
+    bool ok = (es || job.max_iters == 0) ? syndrome_ok() : false;
     int iters = 0;
-    if (!(job.early_stop && ok)) {
+    if (!(es && ok)) {
       if constexpr (MB == 2) {
         init_wide();
         slot_sync(bar_id, nthr);
@@ -644,8 +693,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         if constexpr (MB == 2) vnp_wide(false, k < job.max_iters); else vnp(false, k < job.max_iters);
         slot_sync(bar_id, nthr);
         iters = k;
-        ok = syndrome_ok();
-        if (job.early_stop && ok) break;
+        if (es || k == job.max_iters) ok = syndrome_ok();
+        if (es && ok) break;
       }
     }
     for (int i = stid; i < job.n; i += nthr) job.out_sym[(size_t)frame * job.n + i] = chat[i];
@@ -665,14 +714,19 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 #ifndef NBLDPC_MINB_64
 #define NBLDPC_MINB_64 4
 #endif
+#ifndef NBLDPC_MINB_WIDE
+#define NBLDPC_MINB_WIDE 2
+#endif
 template <int QSEL, int VSEL> struct MinBlocks {
-  static constexpr int v = (QSEL == 0 || QSEL >= 128) ? 2 : (QSEL == 64 ? (VSEL == 1 ? 3 : NBLDPC_MINB_64) : 4);
+  static constexpr int v = QSEL == 0 ? 2 : QSEL >= 128 ? NBLDPC_MINB_WIDE
+                         : (QSEL == 64 ? (VSEL == 1 ? 3 : NBLDPC_MINB_64) : 4);
 };
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
 template <int Q, int VSEL, int MB, bool T1 = false>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
-                                               uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
+                                               uint8_t* chat, unsigned char* scratch, int stid, int nthr,
+                                               int bar_id) {
   if constexpr (VSEL >= 0) {
     decode_frame<Geo<Q, VSEL>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (job.variant == 0) {
