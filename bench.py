@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="default line: skip the probe, the other workloads, the mixed batch and serving")
     ap.add_argument("--probe-seconds", type=float, default=0.6, help="peak: seconds per probe form")
+    ap.add_argument("--probe-rounds", type=int, default=0,
+                    help="peak: fixed rounds per launch, one launch per form (no calibration)")
+    ap.add_argument("--probe-forms", default="", help="peak: comma-separated probe forms (default: all)")
     return ap.parse_args()
 
 
@@ -291,12 +294,13 @@ def sm_count(dev) -> int:
     return torch.cuda.get_device_properties(dev).multi_processor_count
 
 
-def run_probe_form(binding, form, seconds, dev, stream):
-    """One probe launch of about `seconds` (the round count calibrated on shorter launches)."""
+def run_probe_form(binding, form, seconds, dev, stream, fixed_rounds=0):
+    """One probe launch of about `seconds` (the round count calibrated on shorter launches),
+    or of `fixed_rounds` rounds."""
     sink = torch.zeros(1, dtype=torch.int32, device=dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    rounds, cap = 64, 1 << 26
-    for _ in range(10):
+    rounds, cap = (fixed_rounds or 64), 1 << 26
+    for _ in range(0 if fixed_rounds else 10):
         a.record(stream)
         binding.nbldpc_probe_minmax(form, rounds, sink, stream=stream)
         b.record(stream)
@@ -313,7 +317,7 @@ def run_probe_form(binding, form, seconds, dev, stream):
     return {"pairs_per_s": pairs / (ms / 1e3), "ms": ms, "rounds": rounds, "blocks": blocks}
 
 
-def measure_peak(binding, dev, local, seconds, forms=PROBE_FORMS + CONV_FORMS):
+def measure_peak(binding, dev, local, seconds, forms=PROBE_FORMS + CONV_FORMS, fixed_rounds=0):
     """Min-max pairs per clock per SM of each probe form, using the SM clock
     sampled while the probes ran (time x median MHz); the best register form
     is the integer peak of the roofline."""
@@ -322,12 +326,12 @@ def measure_peak(binding, dev, local, seconds, forms=PROBE_FORMS + CONV_FORMS):
     res = {}
     with ClockSampler(local) as clk:
         for label, form in forms:
-            res[label] = run_probe_form(binding, form, seconds, dev, stream)
+            res[label] = run_probe_form(binding, form, seconds, dev, stream, fixed_rounds)
     clocks = clk.summary() or {}
     mhz = clocks.get("sm_mhz") or sm_max_mhz()[0]
     for r in res.values():
         r["pairs_per_clk_sm"] = r["pairs_per_s"] / (sms * mhz * 1e6)
-    reg = [lab for lab, _ in PROBE_FORMS if lab in res]
+    reg = [lab for lab, _ in PROBE_FORMS if lab in res] or list(res)
     best = max(reg, key=lambda k: res[k]["pairs_per_clk_sm"])
     return {"forms": res, "best_form": best, "pairs_per_clk_sm": res[best]["pairs_per_clk_sm"], "sms": sms,
             "clock_mhz_used": mhz, "clocks": clocks}
@@ -363,7 +367,11 @@ def run_peak(args, ws, rank, local):
         return 0
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    meas = measure_peak(binding, dev, local, args.probe_seconds)
+    forms = PROBE_FORMS + CONV_FORMS
+    if args.probe_forms:
+        want = args.probe_forms.split(",")
+        forms = tuple(f for f in forms if f[0] in want)
+    meas = measure_peak(binding, dev, local, args.probe_seconds, forms, args.probe_rounds)
     peak, kind, issue = alu_peaks(meas, dev)
     line = {"metric": "integer min/max throughput (min-max pairs per clock per SM)",
             "value": meas["pairs_per_clk_sm"], "unit": "pairs/clk/SM", "n_gpus": 1, "steps": 1, "warmup": 1,
