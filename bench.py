@@ -530,8 +530,8 @@ def run_mixed(args, ws, rank, local, emit=True, steps=None, warmup=None, peaks=N
         outs.append((torch.empty((f, code.n), dtype=torch.uint8, device=dev),
                      torch.empty((f,), dtype=torch.int32, device=dev),
                      torch.empty((f,), dtype=torch.uint8, device=dev)))
-    steps = steps or steps
-    warmup = warmup or warmup
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     jobs = [(d.handle, g, g.shape[0], max_iters, 1, *o) for d, g, o in zip(decs, gam, outs)]
     wsb = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
