@@ -194,13 +194,19 @@ int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev,
 
 /*
  * ---- Tuning ----------------------------------------------------------------
- * Two knobs per code change speed, never results: the layout variant (0 or
- * 1: how the q x q min-max work of one convolution is split between the lanes
- * of a group and their registers) and the frames decoded side by side in one
- * 256-thread block (1, 2, 4 or 8; small codes leave threads idle at 1).
- * nbldpc_code_create picks a default variant per field order and a frames-per-block value from the
- * code size; nbldpc_code_autotune measures every valid pair on the caller's
- * frames and keeps the fastest.
+ * Two knobs per code change speed, never results: the variant and the frames
+ * decoded side by side in one 256-thread block (1, 2, 4 or 8; small codes
+ * leave threads idle at 1).  Variant bit 0 is the layout (how the q x q
+ * min-max work of one convolution is split between the lanes of a group and
+ * their registers); bit 1 keeps each frame's messages in shared memory instead
+ * of a workspace slot (variants 2 and 3: 8-bit messages, minimal schedule,
+ * q >= 16, one frame per block of 384 threads, and the messages must fit
+ * beside the block's other shared data; otherwise NBLDPC_ERR_UNSUPPORTED).
+ * The workspace of such a code is 256 bytes; mixed-code batches use the
+ * layout bit only.  nbldpc_code_create picks a default variant per field
+ * order and a frames-per-block value from the code size;
+ * nbldpc_code_autotune measures every valid pair on the caller's frames and
+ * keeps the fastest.
  */
 typedef struct nbldpc_tune_result {
   int variant;
@@ -210,8 +216,10 @@ typedef struct nbldpc_tune_result {
 
 int nbldpc_code_get_tuning(const nbldpc_code *code, int *variant, int *frames_per_block);
 
-/* Set the tuning by hand; NBLDPC_ERR_UNSUPPORTED if that pair does not fit the device.  Not
- * concurrent with any other call on the same handle (a decode reads the tuning). */
+/* Set the tuning by hand (variant 0..3, frames_per_block 1, 2, 4 or 8); NBLDPC_ERR_UNSUPPORTED if
+ * that pair does not fit the device or the code.  Not concurrent with any other call on the same
+ * handle (a decode reads the tuning).  Switching a code to 16-bit messages or to the Table 1
+ * schedule drops bit 1 of its variant. */
 int nbldpc_code_set_tuning(nbldpc_code *code, int variant, int frames_per_block);
 
 /* Device workspace nbldpc_code_autotune needs for `frames` tuning frames. */

@@ -24,7 +24,8 @@ struct Plan {
   int per_sm = 0;       // resident blocks per SM
   int grid_max = 0;     // resident blocks on the device
   int blob_cap = 0, n_cap = 0;
-  size_t slot_bytes = 0;  // message slot per frame slot
+  size_t slot_bytes = 0;  // message slot per frame slot in the workspace (0: messages in shared memory)
+  int xs_off = 0;         // shared-memory offset of the messages (resident launches)
 };
 
 extern std::atomic<uint64_t> g_launches;   // decode-kernel launches (nbldpc_kernel_launch_count)

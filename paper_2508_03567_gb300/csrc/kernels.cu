@@ -13,14 +13,24 @@
 
 namespace nbldpc {
 
-// Address of the decode kernel for layout variant v, mb-byte messages and the
-// check-node schedule t1 (1: Table 1's 3 d_c - 4 convolutions, 8-bit messages
-// only) of this unit's field order; null when there is none.
+// Address of the decode kernel for variant v (bit 0: layout; bit 1: messages
+// resident in shared memory), mb-byte messages and the check-node schedule t1
+// (1: Table 1's 3 d_c - 4 convolutions, 8-bit messages only) of this unit's
+// field order; null when there is none.
 const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1) {
 #if NBLDPC_KQ == 0
   (void)v;
   return (mb == 1 && !t1) ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
 #else
+  if (v >= 2) {
+#if NBLDPC_KQ >= 16
+    if (mb != 1 || t1) return nullptr;
+    return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, false, true>)
+                   : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1, false, true>);
+#else
+    return nullptr;
+#endif
+  }
   if (t1) {
     if (mb != 1) return nullptr;
     return v ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, true>)

@@ -125,13 +125,15 @@ template <int Q_, int V_> struct Geo {
 // Of the XN * AWN maxima of one shuffle step, FmaEighths eighths use
 // vmax2_fma (the rest the ALU pipe, which also takes every minimum).  Measured
 // on GB300: 3/8 is best for q <= 64 (GF(64) step: 5/16 435.6, 6/16 437.5,
-// 7/16 434.9, 8/16 430.4 Mbit/s); 1/8 for q >= 128 (four-code batch, 90 % of
-// its work in GF(256): 0 89.5, 1/8 91.5, 2/8 87.7, 3/8 83.2 Mbit/s).
+// 7/16 434.9, 8/16 430.4 Mbit/s; again with the current frame decoder: 2/8
+// and 4/8 2-3 % slower than 3/8); 2/8 for q >= 128 since the convolution's
+// chunk loop is rolled (GF(256) (2,6) N=384: 0, 1/8, 2/8 at 162.2, 150.2,
+// 145.0 ms; before that 1/8 was best).
 #ifndef NBLDPC_FMA_EIGHTHS
 #define NBLDPC_FMA_EIGHTHS 3
 #endif
 #ifndef NBLDPC_FMA_EIGHTHS_WIDE
-#define NBLDPC_FMA_EIGHTHS_WIDE 1
+#define NBLDPC_FMA_EIGHTHS_WIDE 2
 #endif
 template <int Q> struct FmaEighths {
   static constexpr int v = Q >= 128 ? NBLDPC_FMA_EIGHTHS_WIDE : NBLDPC_FMA_EIGHTHS;
@@ -165,6 +167,39 @@ template <class g> __device__ __forceinline__ ConvLane conv_lane(int s, int l) {
 // xh = r ^ (s << TB), which makes the B register index r ^ t independent of
 // the lane and lets the final reduce-scatter keep and send fixed slots.
 // Inputs and output must not alias; the caller syncs the group afterwards.
+//
+// When the shuffle steps span several chunks of B registers (q >= 128), the
+// chunk loop is kept rolled (NBLDPC_CONV_ROLL): the fully unrolled q = 256
+// convolution, inlined at each call site, no longer fits the instruction
+// cache.  The rolled form starts the accumulators at the maximum and shuffles
+// at offset 0 in the first step, so every step has the same code.
+#ifndef NBLDPC_CONV_ROLL
+#define NBLDPC_CONV_ROLL 1
+#endif
+template <class g> __device__ __forceinline__ void load_b_chunk(const uint32_t* __restrict__ B, int c0,
+                                                                uint32_t (&bl)[g::DC][g::XN]) {
+#pragma unroll
+  for (int j = 0; j < g::XN; ++j) {
+    const uint32_t* row = B + j * g::DS + c0;
+    if constexpr (g::DC % 4 == 0) {
+#pragma unroll
+      for (int dd = 0; dd < g::DC; dd += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(row + dd);
+        bl[dd][j] = v.x; bl[dd + 1][j] = v.y; bl[dd + 2][j] = v.z; bl[dd + 3][j] = v.w;
+      }
+    } else if constexpr (g::DC % 2 == 0) {
+#pragma unroll
+      for (int dd = 0; dd < g::DC; dd += 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(row + dd);
+        bl[dd][j] = v.x; bl[dd + 1][j] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int dd = 0; dd < g::DC; ++dd) bl[dd][j] = row[dd];
+    }
+  }
+}
+
 template <class g, bool FMA_MAX>
 __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
                                         uint16_t* __restrict__ C, const ConvLane& ln, unsigned gmask) {
@@ -173,29 +208,34 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
   for (int t = 0; t < g::AWN; ++t) aown[t] = __byte_perm(A[ln.a_off + t * g::DS], 0, ln.sel);
   uint32_t acc[g::XN];
 
+  if constexpr (NBLDPC_CONV_ROLL && g::DS / g::DC > 1) {
+#pragma unroll
+    for (int r = 0; r < g::XN; ++r) acc[r] = 0xFFFFFFFFu;
+#pragma unroll 1
+    for (int c0 = 0; c0 < g::DS; c0 += g::DC) {
+      uint32_t bl[g::DC][g::XN];
+      load_b_chunk<g>(B, c0, bl);
+#pragma unroll
+      for (int dd = 0; dd < g::DC; ++dd) {
+        const int d = 2 * (c0 + dd);
+        uint32_t a[g::AWN];
+#pragma unroll
+        for (int t = 0; t < g::AWN; ++t) a[t] = __shfl_xor_sync(gmask, aown[t], d);
+#pragma unroll
+        for (int r = 0; r < g::XN; ++r)
+#pragma unroll
+          for (int t = 0; t < g::AWN; ++t) {
+            const uint32_t m = (FMA_MAX && r * g::AWN + t < FmaMax<g>::v) ? vmax2_fma(a[t], bl[dd][r ^ t])
+                                                                : vmax2(a[t], bl[dd][r ^ t]);
+            acc[r] = vmin2(acc[r], m);
+          }
+      }
+    }
+  } else {
 #pragma unroll
   for (int c0 = 0; c0 < g::DS; c0 += g::DC) {
     uint32_t bl[g::DC][g::XN];
-#pragma unroll
-    for (int j = 0; j < g::XN; ++j) {
-      const uint32_t* row = B + j * g::DS + c0;
-      if constexpr (g::DC % 4 == 0) {
-#pragma unroll
-        for (int dd = 0; dd < g::DC; dd += 4) {
-          const uint4 v = *reinterpret_cast<const uint4*>(row + dd);
-          bl[dd][j] = v.x; bl[dd + 1][j] = v.y; bl[dd + 2][j] = v.z; bl[dd + 3][j] = v.w;
-        }
-      } else if constexpr (g::DC % 2 == 0) {
-#pragma unroll
-        for (int dd = 0; dd < g::DC; dd += 2) {
-          const uint2 v = *reinterpret_cast<const uint2*>(row + dd);
-          bl[dd][j] = v.x; bl[dd + 1][j] = v.y;
-        }
-      } else {
-#pragma unroll
-        for (int dd = 0; dd < g::DC; ++dd) bl[dd][j] = row[dd];
-      }
-    }
+    load_b_chunk<g>(B, c0, bl);
 #pragma unroll
     for (int dd = 0; dd < g::DC; ++dd) {
       const int d = 2 * (c0 + dd);
@@ -211,6 +251,7 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
           acc[r] = (d == 0 && t == 0) ? m : vmin2(acc[r], m);
         }
     }
+  }
   }
   // reduce-scatter over the SB lane bits: keep slot r, receive the partner's r | 2^c
 #pragma unroll
@@ -261,7 +302,12 @@ struct LaunchParams {
   int fpb;                    // frame slots per block (blockDim / fpb threads each)
   int slot_smem;              // shared bytes per frame slot
   int blob_cap, n_cap;        // largest code blob and N among the jobs
+  int xs_off;                 // resident launches: shared-memory offset of the slot's messages
 };
+
+// Threads of a block whose frame keeps its messages in shared memory (two
+// blocks per SM: the same 24 warps as three 256-thread blocks).
+constexpr int kResidentThreads = 384;
 
 
 // Check-node permutation by scatter from registers (8-bit messages, 16 <= q <=
@@ -555,6 +601,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     // XOR sums of the h x^b = exp2[log h + b]
     auto scatter_piece = [&](bool first, int e0, int c) {
       const int j = c / CH, part = c - j * CH;
+      // gamma on the first pass, else the edge's message row (through one pointer: a separate
+      // read-only load of gamma measured 2 % slower at GF(64))
       const uint8_t* src = first ? gam + (size_t)edge_col[e0 + j] * Q : X + (size_t)(e0 + j) * Q;
       const uint4 v = reinterpret_cast<const uint4*>(src)[part];
       const int lh = edge_lh[e0 + j];
@@ -738,8 +786,12 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
 
 // MB: message bytes per symbol (1: 8-bit messages; 2: 16-bit, single-field kernels only).
 // T1: the Table 1 check-node schedule (3 d_c - 4 convolutions; single-field kernels only).
-template <int QSEL, int VSEL, int MB, bool T1 = false>
-__global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kernel(const __grid_constant__ LaunchParams p) {
+// XS: the frame's messages stay in shared memory (8-bit messages, 16 <= q,
+// single-field kernels; kResidentThreads threads, one frame per block).
+template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false>
+__global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : MinBlocks<QSEL, VSEL>::v)
+    mma_decode_kernel(const __grid_constant__ LaunchParams p) {
+  static_assert(!XS || (QSEL >= 16 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, q >= 16");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
   const int slot = threadIdx.x / nthr, stid = threadIdx.x % nthr;
@@ -749,7 +801,7 @@ __global__ void __launch_bounds__(256, MinBlocks<QSEL, VSEL>::v) mma_decode_kern
   uint8_t* chat = base + p.blob_cap;
   volatile int* ctl = reinterpret_cast<volatile int*>(base + p.blob_cap + p.n_cap);
   unsigned char* scratch = base + p.blob_cap + p.n_cap + 16;
-  uint8_t* X = p.msg + ((size_t)blockIdx.x * p.fpb + slot) * p.slot_bytes;
+  uint8_t* X = XS ? base + p.xs_off : p.msg + ((size_t)blockIdx.x * p.fpb + slot) * p.slot_bytes;
   int staged = -1;
 
   for (;;) {

@@ -68,8 +68,8 @@ namespace {
 // the Table 1 check-node schedule (each a separate kernel instantiation).
 int kmode(const nbldpc_code* c) { return c->mb == 2 ? 2 : (c->cnp_schedule == NBLDPC_CNP_TABLE1 ? 3 : 1); }
 
-// kernel compiled for one field order, layout variant and kernel mode, or for
-// every field order (q = 0, mode 1)
+// kernel compiled for one field order, variant (bit 0: layout; bit 1: messages
+// resident in shared memory) and kernel mode, or for every field order (q = 0, mode 1)
 const void* kernel_for(int q, int v, int km) {
   const int mb = km == 2 ? 2 : 1, t1 = km == 3 ? 1 : 0;
   switch (q) {
@@ -118,10 +118,12 @@ int group_bytes(int q, int dmax, int mb) {
 
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
-bool g_attr_done[64][49] = {};
+bool g_attr_done[64][65] = {};
 
+// per field order: 3 kernel modes x 2 layouts, then the 2 resident-message kernels
 int kernel_slot(int q, int v, int km) {
-  return q == 0 ? 0 : 1 + 6 * (nbldpc::ilog2(q) - 1) + 2 * (km - 1) + (v ? 1 : 0);
+  if (q == 0) return 0;
+  return 1 + 8 * (nbldpc::ilog2(q) - 1) + (v >= 2 ? 6 + (v & 1) : 2 * (km - 1) + (v & 1));
 }
 
 int prepare_kernel(int q, int v, int km, int dev, int smem_optin) {
@@ -148,21 +150,26 @@ CodeNeeds needs_of(const nbldpc_code* c, int variant, int mb) {
 }
 
 // Plan a launch of kernel (kq, kv, kernel mode km) with fpb frame slots per block for a set of codes.
+// Variants 2 and 3 keep each frame's messages in shared memory: one frame per
+// block of nbldpc::kResidentThreads threads, no message slots in the workspace.
 int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return NBLDPC_ERR_CUDA;
-  if (fpb < 1 || kThreads % fpb) return NBLDPC_ERR_ARG;
-  const int nthr = kThreads / fpb;
+  const bool resident = kv >= 2;
+  const int threads = resident ? nbldpc::kResidentThreads : kThreads;
+  if (fpb < 1 || threads % fpb) return NBLDPC_ERR_ARG;
+  if (resident && (fpb != 1 || km != 1 || kq < 16)) return NBLDPC_ERR_UNSUPPORTED;
+  const int nthr = threads / fpb;
   if (nthr < 32) return NBLDPC_ERR_UNSUPPORTED;
   Plan pl{};
   pl.fpb = fpb;
-  pl.threads = kThreads;
+  pl.threads = threads;
   int scratch = 0;
   for (int i = 0; i < nc; ++i) {
-    const int G = group_lanes(cs[i].q, cs[i].variant);
+    const int G = group_lanes(cs[i].q, cs[i].variant & 1);
     if (G > nthr) return NBLDPC_ERR_UNSUPPORTED;
     const int s = (nthr / G) * group_bytes(cs[i].q, cs[i].dmax, cs[i].mb);
     if (s > scratch) scratch = s;
@@ -173,6 +180,11 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
   pl.blob_cap = (int)round_up((size_t)pl.blob_cap, 16);
   pl.n_cap = (int)round_up((size_t)pl.n_cap, 16);
   pl.slot_smem = (int)round_up((size_t)(pl.blob_cap + pl.n_cap + 16 + scratch), 16);
+  if (resident) {   // the messages follow the slot's scratch
+    pl.xs_off = pl.slot_smem;
+    pl.slot_smem += (int)round_up(pl.slot_bytes, 16);
+    pl.slot_bytes = 0;
+  }
   pl.smem = fpb * pl.slot_smem;
   if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
   int st = prepare_kernel(kq, kv, km, dev, optin);
@@ -186,14 +198,15 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
   return NBLDPC_OK;
 }
 
-// Layout variant when nothing better is known: the one the autotuner picked for
-// the benchmark codes on GB300 (GF(16), GF(32), GF(64): variant 1).
-int default_variant(int q) { return (q >= 16 && q <= 64) ? 1 : 0; }
+// Variant when nothing better is known: the one measured fastest for the
+// benchmark codes on GB300 (GF(16), GF(32): layout 1; GF(64): layout 1 with
+// the messages in shared memory; otherwise layout 0).
+int default_variant(int q) { return q == 64 ? 3 : (q >= 16 && q <= 32) ? 1 : 0; }
 
 // Frame slots per block when nothing better is known: enough threads per slot
 // for the checks and variable nodes of one frame, at least one warp.
 int default_fpb(const nbldpc_code* c) {
-  const int G = group_lanes(c->q, default_variant(c->q));
+  const int G = group_lanes(c->q, default_variant(c->q) & 1);
   const int work = c->m * G;
   int fpb = 1;
   while (fpb < 8 && kThreads / (2 * fpb) >= 32 && kThreads / (2 * fpb) >= work && kThreads / (2 * fpb) >= G) fpb *= 2;
@@ -225,7 +238,7 @@ nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames,
   j.n = c->n;
   j.m = c->m;
   j.dmax = c->dmax;
-  j.variant = c->variant;
+  j.variant = c->variant & 1;          // layout (a mixed-code kernel keeps messages in the workspace)
   j.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
   j.group_bytes = group_bytes(c->q, c->dmax, c->mb);
   j.frames = frames;
@@ -246,6 +259,7 @@ int launch_plan(const void* kernel, const Plan& pl, nbldpc::LaunchParams& lp, in
   lp.slot_smem = pl.slot_smem;
   lp.blob_cap = pl.blob_cap;
   lp.n_cap = pl.n_cap;
+  lp.xs_off = pl.xs_off;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
   void* args[] = {&lp};
@@ -298,11 +312,13 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
   int st = check_device(c);
   if (st != NBLDPC_OK) return st;
   const Plan& pl = c->plan;
-  const size_t per_block = (size_t)pl.fpb * pl.slot_bytes;
+  const size_t per_block = (size_t)pl.fpb * pl.slot_bytes;   // 0 when the messages stay in shared memory
   if (256 + per_block > (size_t)NBLDPC_NOALLOC_SCRATCH_BYTES) return NBLDPC_ERR_UNSUPPORTED;
-  const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / per_block);
   int grid = grid_for(pl, frames);
-  if (grid > fit) grid = fit;
+  if (per_block) {
+    const int fit = (int)(((size_t)NBLDPC_NOALLOC_SCRATCH_BYTES - 256) / per_block);
+    if (grid > fit) grid = fit;
+  }
   st = cuda_status(cudaGetLastError());
   if (st != NBLDPC_OK) return st;
   void* scratch = nullptr;
@@ -449,7 +465,13 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   if (e != cudaSuccess) { delete c; return e == cudaErrorMemoryAllocation ? NBLDPC_ERR_NOMEM : NBLDPC_ERR_CUDA; }
   e = cudaMemcpy(c->blob_dev, blob.data(), o, cudaMemcpyHostToDevice);
   int st = cuda_status(e);
-  if (st == NBLDPC_OK) st = configure(c, default_variant(q), default_fpb(c));
+  if (st == NBLDPC_OK) {
+    // the resident-message form takes one frame per block and must fit shared memory;
+    // otherwise the same layout with the messages in the workspace
+    const int v = default_variant(q), fpb = default_fpb(c);
+    st = (v >= 2 && fpb == 1) ? configure(c, v, fpb) : NBLDPC_ERR_UNSUPPORTED;
+    if (st == NBLDPC_ERR_UNSUPPORTED) st = configure(c, v & 1, fpb);
+  }
   if (st == NBLDPC_OK) {
     c->fft_status = fft_configure(c);
     if (c->fft_status == NBLDPC_ERR_CUDA) st = NBLDPC_ERR_CUDA;
@@ -489,7 +511,7 @@ int nbldpc_code_get_tuning(const nbldpc_code* c, int* variant, int* frames_per_b
 }
 
 int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
-  if (!c || variant < 0 || variant > 1 || frames_per_block < 1 || frames_per_block > 8 ||
+  if (!c || variant < 0 || variant > 3 || frames_per_block < 1 || frames_per_block > 8 ||
       (frames_per_block & (frames_per_block - 1)))
     return NBLDPC_ERR_ARG;
   const int st = check_device(c);
@@ -503,7 +525,9 @@ int nbldpc_code_set_message_bits(nbldpc_code* c, int bits) {
   if (check_device(c) != NBLDPC_OK) return check_device(c);
   const int old = c->mb;
   c->mb = bits / 8;
-  const int st = configure(c, c->variant, c->plan.fpb);
+  // resident messages serve 8-bit codes only: a 16-bit code keeps the layout in the workspace form
+  const int v = c->mb == 1 ? c->variant : c->variant & 1;
+  const int st = configure(c, v, v == c->variant ? c->plan.fpb : 1);
   if (st != NBLDPC_OK) c->mb = old;
   return st;
 }
@@ -520,7 +544,9 @@ int nbldpc_code_set_cnp_schedule(nbldpc_code* c, int schedule) {
   if (check_device(c) != NBLDPC_OK) return check_device(c);
   const int old = c->cnp_schedule;
   c->cnp_schedule = schedule;
-  const int st = configure(c, c->variant, c->plan.fpb);   // the schedule is a separate kernel
+  // the schedule is a separate kernel; resident messages serve the minimal schedule only
+  const int v = schedule == NBLDPC_CNP_MINIMAL ? c->variant : c->variant & 1;
+  const int st = configure(c, v, v == c->variant ? c->plan.fpb : 1);
   if (st != NBLDPC_OK) c->cnp_schedule = old;
   return st;
 }
@@ -565,7 +591,7 @@ static int batch_plan(const nbldpc_job* jobs, int n_jobs, Plan* pl, int* total) 
     const int st = check_device(c);
     if (st != NBLDPC_OK) return st;
     if (kmode(c) != 1) return NBLDPC_ERR_UNSUPPORTED;   // mixed-code launches: 8-bit messages, minimal schedule
-    need[i] = needs_of(c, c->variant, 1);
+    need[i] = needs_of(c, c->variant & 1, 1);
     if (c->plan.fpb < fpb) fpb = c->plan.fpb;
     t += jobs[i].frames;
   }
@@ -617,7 +643,7 @@ static size_t tune_outputs(const nbldpc_code* c, int frames) {
 int nbldpc_code_autotune_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
   if (!c || !bytes || frames < 1) return NBLDPC_ERR_ARG;
   size_t mx = 0;
-  for (int v = 0; v < 2; ++v)
+  for (int v = 0; v < 4; ++v)
     for (int fpb = 1; fpb <= 8; fpb *= 2) {
       Plan pl{};
       const CodeNeeds need = needs_of(c, v, c->mb);
@@ -653,7 +679,7 @@ int nbldpc_code_autotune(nbldpc_code* c, const uint8_t* gamma_dev, int frames, i
   int best_v = v_old, best_f = f_old, count = 0;
   float best = 3.4e38f;
   st = NBLDPC_OK;
-  for (int v = 0; v < 2 && st == NBLDPC_OK; ++v)
+  for (int v = 0; v < 4 && st == NBLDPC_OK; ++v)
     for (int fpb = 1; fpb <= 8 && st == NBLDPC_OK; fpb *= 2) {
       if (configure(c, v, fpb) != NBLDPC_OK) continue;
       // one untimed decode, then one timed decode with fixed iterations

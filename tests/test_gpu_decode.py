@@ -254,8 +254,8 @@ def test_every_variant_and_frames_per_block(name, shape):
     want = oracle.decode(code, g, 8, 1, threads=THREADS)
     dec = binding.Decoder.from_code(code)
     gd = torch.as_tensor(g).cuda()
-    tried = 0
-    for v in (0, 1):
+    tried, resident = 0, 0
+    for v in (0, 1, 2, 3):             # bit 1: messages resident in shared memory (q >= 16, one frame per block)
         for fpb in (1, 2, 4, 8):
             try:
                 dec.set_tuning(v, fpb)
@@ -266,7 +266,9 @@ def test_every_variant_and_frames_per_block(name, shape):
             got = [t.cpu().numpy() for t in dec.decode(gd, 8, 1)]
             assert_same(got, want, f"{name} variant {v} fpb {fpb}")
             tried += 1
+            resident += v >= 2
     assert tried >= 2
+    assert resident == (2 if code.q >= 16 else 0)
 
 
 def test_autotune_picks_a_valid_pair_and_keeps_results():
