@@ -126,14 +126,15 @@ template <int Q_, int V_> struct Geo {
 // vmax2_fma (the rest the ALU pipe, which also takes every minimum).  Measured
 // on GB300: 3/8 is best for q <= 64 (GF(64) step: 5/16 435.6, 6/16 437.5,
 // 7/16 434.9, 8/16 430.4 Mbit/s; again with the current frame decoder: 2/8
-// and 4/8 2-3 % slower than 3/8); 2/8 for q >= 128 since the convolution's
-// chunk loop is rolled (GF(256) (2,6) N=384: 0, 1/8, 2/8 at 162.2, 150.2,
-// 145.0 ms; before that 1/8 was best).
+// and 4/8 2-3 % slower than 3/8); 3/8 for q >= 128 too since the
+// convolution's chunk loop is rolled (GF(256) (2,6) N=384, layout 0: 0 to
+// 5/8 at 162.2, 150.2, 145.0, 142.5, 148.7, 167.5 ms; before the loop was
+// rolled 1/8 was best).
 #ifndef NBLDPC_FMA_EIGHTHS
 #define NBLDPC_FMA_EIGHTHS 3
 #endif
 #ifndef NBLDPC_FMA_EIGHTHS_WIDE
-#define NBLDPC_FMA_EIGHTHS_WIDE 2
+#define NBLDPC_FMA_EIGHTHS_WIDE 3
 #endif
 template <int Q> struct FmaEighths {
   static constexpr int v = Q >= 128 ? NBLDPC_FMA_EIGHTHS_WIDE : NBLDPC_FMA_EIGHTHS;
