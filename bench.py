@@ -389,6 +389,13 @@ def run_peak(args, ws, rank, local):
 L2_BYTES = 129e6
 
 
+def batch_pool(step_bytes: float) -> int:
+    """Distinct batches a workload rotates through so that the inputs of one timed
+    decode are not in L2: 1 when one step's inputs exceed L2, else enough batches
+    for twice the L2 size."""
+    return 1 if step_bytes > L2_BYTES else int(np.ceil(2 * L2_BYTES / step_bytes))
+
+
 def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, frames=None, graph=False,
                      cpu_frames=None, e2e=True, profile=None):
     """One min-max workload of inputs.WORKLOADS through nbldpc_decode: its frames
@@ -405,7 +412,7 @@ def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, f
     fpp = frames or w["frames"]
     npts = len(w["ebn0"])
     step_bytes = npts * fpp * code.n * code.q
-    pool = 1 if step_bytes > L2_BYTES else int(np.ceil(2 * L2_BYTES / step_bytes))
+    pool = batch_pool(step_bytes)
     gam, cws = [], []
     for i, eb in enumerate(w["ebn0"]):
         bt = I.make_batch(code, eb, I.workload_seed(name, i), pool * fpp, device=dev, chunk=65536)

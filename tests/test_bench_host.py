@@ -168,3 +168,30 @@ def test_command_line_lists_every_workload():
                          text=True, check=True).stdout
     for mode in ("gf64", "mixed", "serving", "width", "fftspa", "schedule"):
         assert mode in out
+
+
+def test_measured_peak_and_issue_bound_arithmetic(monkeypatch):
+    """The roofline denominators: the probe's best pairs/clk/SM x 2 u16 ops x SMs x the maximum
+    SM clock, beside the issue-bound 256 ops/clk/SM; frac and frac_issue_bound divide by them."""
+    monkeypatch.setattr(bench, "sm_count", lambda dev: 152)
+    monkeypatch.setattr(bench, "sm_max_mhz", lambda: (2070.0, "measured"))
+    meas = {"pairs_per_clk_sm": 88.0, "best_form": "fma_3_8"}
+    peak, kind, issue = bench.alu_peaks(meas, None)
+    assert peak == pytest.approx(152 * 2 * 88.0 * 2070e6 / 1e9)
+    assert issue == pytest.approx(152 * 256 * 2070e6 / 1e9)
+    assert "measured" in kind and "fma_3_8" in kind
+    peak0, kind0, issue0 = bench.alu_peaks(None, None)
+    assert peak0 == issue0 and kind0.startswith("derived")
+    r = bench.roofline_alu(0.5 * peak, peak, kind, issue)
+    assert r["frac"] == pytest.approx(0.5) and r["frac_issue_bound"] == pytest.approx(0.5 * peak / issue)
+    assert r["bound"] == "alu" and r["unit"] == "Gop/s"
+
+
+def test_small_workloads_rotate_through_more_than_l2():
+    """A step whose inputs fit L2 rotates through distinct batches totalling more than L2;
+    a step larger than L2 is decoded as it is."""
+    gf4 = 1000 * 48 * 4                       # GF(4) N=48, 1000 frames
+    n = bench.batch_pool(gf4)
+    assert n > 1 and n * gf4 > bench.L2_BYTES and (n - 1) * gf4 < 2 * bench.L2_BYTES
+    assert bench.batch_pool(196608 * 576 * 64) == 1   # the GF(64) step
+    assert bench.batch_pool(16384 * 384 * 256) == 1   # GF(256) N=384, 16384 frames
