@@ -414,7 +414,6 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // ---------------------------------------------------------------- one frame
-
 // Decodes frame `frame` of `job` with the nthr threads of one frame slot
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
@@ -443,9 +442,11 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   const unsigned gmask = group_mask<g::G>(lane);
   const ConvLane cl = conv_lane<g>(gl >> g::LB, gl & (g::DN - 1));
   // variable-node groups (VG lanes per variable node)
-  const int vgrp = stid / g::VG, nvgroups = nthr / g::VG;
-  const int vgl = stid % g::VG;
-  const unsigned vmask = group_mask<g::VG>(lane);
+  // (16-bit messages keep at most 8 symbols per lane: their rows are read symbol by symbol)
+  constexpr int VBPL = (MB == 2 && g::VBPL > 8) ? 8 : g::VBPL, VG = Q / VBPL, VW = VBPL / 2;
+  const int vgrp = stid / VG, nvgroups = nthr / VG;
+  const int vgl = stid % VG;
+  const unsigned vmask = group_mask<VG>(lane);
 
   // lane constants for the gather permutation (staged rows): logarithms of the
   // symbols this lane gathers, packed 8 bits per symbol; the zero symbol, which
@@ -482,7 +483,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     // subtractions never carry or borrow across the halves.
     // 16-bit messages: the same pass on 32-bit sums, one symbol per register
     auto vnp_wide = [&](bool first, bool want_alpha) {
-      constexpr int NB = g::VBPL;
+      constexpr int NB = VBPL;
       for (int vn = vgrp; vn < job.n; vn += nvgroups) {
         int S[NB];
         const uint8_t* gr = gam + (size_t)vn * Q + vgl * NB;
@@ -499,7 +500,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         int key = 0x7FFFFFFF;
 #pragma unroll
         for (int i = 0; i < NB; ++i) key = min(key, (S[i] << 8) | (vgl * NB + i));
-        key = group_min<g::VG>(key, vmask);
+        key = group_min<VG>(key, vmask);
         if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
         if (!first && want_alpha) {
           for (int k = k0; k < k1; ++k) {
@@ -508,7 +509,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
             int mn = 0x7FFFFFFF;
 #pragma unroll
             for (int i = 0; i < NB; ++i) { t[i] = S[i] - row[i]; mn = min(mn, t[i]); }
-            mn = group_min<g::VG>(mn, vmask);
+            mn = group_min<VG>(mn, vmask);
 #pragma unroll
             for (int i = 0; i < NB; ++i) row[i] = (uint16_t)min(65535, t[i] - mn);
           }
@@ -527,54 +528,54 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 
     auto vnp = [&](bool first, bool want_alpha) {
       // symbol values of this lane's packed words: (a, a + 1), a = vgl * VBPL + 2 i
-      const uint32_t vsym0 = (uint32_t)(vgl * g::VBPL) * 0x10001u + 0x10000u;
+      const uint32_t vsym0 = (uint32_t)(vgl * VBPL) * 0x10001u + 0x10000u;
       for (int vn = vgrp; vn < job.n; vn += nvgroups) {
-        uint32_t S[g::VW];
-        load_pairs<g::VBPL>(gam + (size_t)vn * Q + vgl * g::VBPL, S);
+        uint32_t S[VW];
+        load_pairs<VBPL>(gam + (size_t)vn * Q + vgl * VBPL, S);
         const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
         if (!first) {
           for (int k = k0; k < k1; ++k) {
-            uint32_t b[g::VW];
-            load_pairs<g::VBPL>(X + (size_t)vn_edge[k] * Q + vgl * g::VBPL, b);
+            uint32_t b[VW];
+            load_pairs<VBPL>(X + (size_t)vn_edge[k] * Q + vgl * VBPL, b);
 #pragma unroll
-            for (int i = 0; i < g::VW; ++i) S[i] += b[i];
+            for (int i = 0; i < VW; ++i) S[i] += b[i];
           }
         }
         int key;
         if (job.key16) {        // key = S * q + a fits 16 bits: minimum value, lowest symbol
           uint32_t kw = S[0] * (uint32_t)Q + vsym0;
 #pragma unroll
-          for (int i = 1; i < g::VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + (vsym0 + 0x20002u * i));
+          for (int i = 1; i < VW; ++i) kw = vmin2(kw, S[i] * (uint32_t)Q + (vsym0 + 0x20002u * i));
           key = (int)min(kw & 0xFFFFu, kw >> 16);
-          key = group_min<g::VG>(key, vmask);
+          key = group_min<VG>(key, vmask);
           if (vgl == 0) chat[vn] = (uint8_t)(key & (Q - 1));
         } else {
           key = 0x7FFFFFFF;
 #pragma unroll
-          for (int i = 0; i < g::VW; ++i) {
+          for (int i = 0; i < VW; ++i) {
             const uint32_t sy = vsym0 + 0x20002u * i;
             key = min(key, (int)(((S[i] & 0xFFFFu) << 8) | (sy & 0xFFFFu)));
             key = min(key, (int)(((S[i] >> 16) << 8) | (sy >> 16)));
           }
-          key = group_min<g::VG>(key, vmask);
+          key = group_min<VG>(key, vmask);
           if (vgl == 0) chat[vn] = (uint8_t)(key & 0xFF);
         }
         if (!first && want_alpha) {
           for (int k = k0; k < k1; ++k) {
-            uint8_t* row = X + (size_t)vn_edge[k] * Q + vgl * g::VBPL;
-            uint32_t t[g::VW];
-            load_pairs<g::VBPL>(row, t);
+            uint8_t* row = X + (size_t)vn_edge[k] * Q + vgl * VBPL;
+            uint32_t t[VW];
+            load_pairs<VBPL>(row, t);
 #pragma unroll
-            for (int i = 0; i < g::VW; ++i) t[i] = S[i] - t[i];
+            for (int i = 0; i < VW; ++i) t[i] = S[i] - t[i];
             uint32_t mw = t[0];
 #pragma unroll
-            for (int i = 1; i < g::VW; ++i) mw = vmin2(mw, t[i]);
+            for (int i = 1; i < VW; ++i) mw = vmin2(mw, t[i]);
             int mn = (int)min(mw & 0xFFFFu, mw >> 16);
-            mn = group_min<g::VG>(mn, vmask);
+            mn = group_min<VG>(mn, vmask);
             const uint32_t mm = (uint32_t)mn * 0x10001u;
 #pragma unroll
-            for (int i = 0; i < g::VW; ++i) t[i] = vmin2(t[i] - mm, 0x00FF00FFu);
-            store_pairs<g::VBPL>(row, t);
+            for (int i = 0; i < VW; ++i) t[i] = vmin2(t[i] - mm, 0x00FF00FFu);
+            store_pairs<VBPL>(row, t);
           }
         }
       }
