@@ -200,7 +200,7 @@ int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev,
  * min-max work of one convolution is split between the lanes of a group and
  * their registers); bit 1 keeps each frame's messages in shared memory instead
  * of a workspace slot (variants 2 and 3: 8-bit messages, minimal schedule,
- * q >= 16, one frame per block of 384 threads, and the messages must fit
+ * blocks of 384 threads with 1, 2 or 4 frames, and the messages must fit
  * beside the block's other shared data; otherwise NBLDPC_ERR_UNSUPPORTED).
  * The workspace of such a code is 256 bytes; mixed-code batches use the
  * layout bit only.  nbldpc_code_create picks a default variant per field

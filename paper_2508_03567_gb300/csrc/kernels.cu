@@ -23,13 +23,9 @@ const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1) {
   return (mb == 1 && !t1) ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
 #else
   if (v >= 2) {
-#if NBLDPC_KQ >= 16
     if (mb != 1 || t1) return nullptr;
     return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, false, true>)
                    : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1, false, true>);
-#else
-    return nullptr;
-#endif
   }
   if (t1) {
     if (mb != 1) return nullptr;

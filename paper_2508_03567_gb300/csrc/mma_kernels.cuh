@@ -418,7 +418,9 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
 // slot's message area ([nnz][q] bytes).
-template <class g, int MB, bool T1>
+// REG4: q = 4 codes take the register form of the check-node pass (single-field
+// kernels; the all-field kernel keeps the group form).
+template <class g, int MB, bool T1, bool REG4 = true>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
@@ -725,6 +727,76 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       }
     };
 
+    // ---- check-node pass for q = 4 in registers: one lane per check (checks of
+    // degree <= kRegDeg).  A 4-symbol vector is two words of 16-bit values,
+    // (v0, v1), (v2, v3); the coefficient permutations are byte permutes of the
+    // 4-byte rows and the 16-pair convolutions use no shared memory, so the
+    // pass has no memory round trip between its steps (at q = 4 the group form
+    // is a chain of short shared-memory dependencies).
+    constexpr int kRegDeg = 8;
+    // C(x) = min_y max(A(y), B(x ^ y)): B ^ 1 swaps the halves of each word, B ^ 2 swaps the words
+    auto conv4 = [](const uint32_t (&a)[2], const uint32_t (&b)[2], uint32_t (&c)[2]) {
+      const uint32_t a0 = __byte_perm(a[0], 0, 0x1010), a1 = __byte_perm(a[0], 0, 0x3232);
+      const uint32_t a2 = __byte_perm(a[1], 0, 0x1010), a3 = __byte_perm(a[1], 0, 0x3232);
+      const uint32_t s0 = __byte_perm(b[0], 0, 0x1032), s1 = __byte_perm(b[1], 0, 0x1032);
+      c[0] = vmin2(vmin2(vmax2(a0, b[0]), vmax2(a1, s0)), vmin2(vmax2(a2, b[1]), vmax2(a3, s1)));
+      c[1] = vmin2(vmin2(vmax2(a0, b[1]), vmax2(a1, s1)), vmin2(vmax2(a2, b[0]), vmax2(a3, s0)));
+    };
+    auto cnp_regs4 = [&](bool first) {
+      // beta_e(a) = R(h a): byte a of the row from the 16-bit value R(i), i = h a, of the words R
+      auto store_beta = [&](int e, const uint32_t (&R)[2]) {
+        const int lh = edge_lh[e];
+        const int i1 = exp2[lh], i2 = exp2[lh + 1], i3 = i1 ^ i2;
+        const uint32_t sel = (uint32_t)((((i1 >> 1) << 2) | ((i1 & 1) << 1)) << 4) |
+                             (uint32_t)((((i2 >> 1) << 2) | ((i2 & 1) << 1)) << 8) |
+                             (uint32_t)((((i3 >> 1) << 2) | ((i3 & 1) << 1)) << 12);
+        *reinterpret_cast<uint32_t*>(X + (size_t)e * 4) = __byte_perm(R[0], R[1], sel);
+      };
+      for (int r = stid; r < job.m; r += nthr) {
+        const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
+        uint32_t P[kRegDeg][2], F[kRegDeg][2];
+#pragma unroll
+        for (int j = 0; j < kRegDeg; ++j) {
+          if (j < d) {
+            // P_j(y) = alpha_j(h^-1 y): (alpha(0), alpha(h^-1)), (alpha(h^-1 2), alpha(h^-1 3))
+            const int e = e0 + j;
+            const uint32_t row = first ? *reinterpret_cast<const uint32_t*>(gam + (size_t)edge_col[e] * 4)
+                                       : *reinterpret_cast<const uint32_t*>(X + (size_t)e * 4);
+            const int lhinv = edge_lhi[e];
+            const uint32_t s1 = exp2[lhinv], s2 = exp2[lhinv + 1], s3 = s1 ^ s2;
+            P[j][0] = __byte_perm(row, 0, 0x4040u | (s1 << 8));
+            P[j][1] = __byte_perm(row, 0, 0x4040u | s2 | (s3 << 8));
+          }
+        }
+        // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j; beta_{d-1} = F_{d-2}
+        F[0][0] = P[0][0];
+        F[0][1] = P[0][1];
+#pragma unroll
+        for (int j = 1; j < kRegDeg - 1; ++j)
+          if (j <= d - 2) conv4(F[j - 1], P[j], F[j]);
+#pragma unroll
+        for (int j = 0; j < kRegDeg - 1; ++j)
+          if (j == d - 2) store_beta(e0 + d - 1, F[j]);
+        // backward: B_{d-1} = P_{d-1}; beta_j = F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j; beta_0 = B_1
+        uint32_t Bc[2] = {0u, 0u};
+#pragma unroll
+        for (int j = 1; j < kRegDeg; ++j)
+          if (j == d - 1) { Bc[0] = P[j][0]; Bc[1] = P[j][1]; }
+#pragma unroll
+        for (int j = kRegDeg - 2; j >= 1; --j) {
+          if (j <= d - 2) {
+            uint32_t R[2], Bn[2];
+            conv4(F[j - 1], Bc, R);
+            store_beta(e0 + j, R);
+            conv4(Bc, P[j], Bn);
+            Bc[0] = Bn[0];
+            Bc[1] = Bn[1];
+          }
+        }
+        store_beta(e0, Bc);
+      }
+    };
+
     // ---- decode one frame.  Without early stop only the final decision is
     // tested, so the stop test runs once, after the last iteration.
     const bool es = job.early_stop != 0;
@@ -738,7 +810,11 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         slot_sync(bar_id, nthr);
       }
       for (int k = 1; k <= job.max_iters; ++k) {
-        cnp(MB == 1 && k == 1);
+        if constexpr (Q == 4 && MB == 1 && !T1 && REG4) {
+          if (job.dmax <= kRegDeg) cnp_regs4(k == 1); else cnp(k == 1);
+        } else {
+          cnp(MB == 1 && k == 1);
+        }
         slot_sync(bar_id, nthr);
         if constexpr (MB == 2) vnp_wide(false, k < job.max_iters); else vnp(false, k < job.max_iters);
         slot_sync(bar_id, nthr);
@@ -780,20 +856,20 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
   if constexpr (VSEL >= 0) {
     decode_frame<Geo<Q, VSEL>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (job.variant == 0) {
-    decode_frame<Geo<Q, 0>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 0>, MB, T1, false>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else {
-    decode_frame<Geo<Q, 1>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, 1>, MB, T1, false>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   }
 }
 
 // MB: message bytes per symbol (1: 8-bit messages; 2: 16-bit, single-field kernels only).
 // T1: the Table 1 check-node schedule (3 d_c - 4 convolutions; single-field kernels only).
-// XS: the frame's messages stay in shared memory (8-bit messages, 16 <= q,
-// single-field kernels; kResidentThreads threads, one frame per block).
+// XS: the frames' messages stay in shared memory (8-bit messages, single-field
+// kernels; kResidentThreads threads, 1, 2 or 4 frame slots per block).
 template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false>
 __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : MinBlocks<QSEL, VSEL>::v)
     mma_decode_kernel(const __grid_constant__ LaunchParams p) {
-  static_assert(!XS || (QSEL >= 16 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, q >= 16");
+  static_assert(!XS || (QSEL >= 2 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, one field");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
   const int slot = threadIdx.x / nthr, stid = threadIdx.x % nthr;

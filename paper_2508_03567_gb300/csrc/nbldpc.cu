@@ -150,8 +150,9 @@ CodeNeeds needs_of(const nbldpc_code* c, int variant, int mb) {
 }
 
 // Plan a launch of kernel (kq, kv, kernel mode km) with fpb frame slots per block for a set of codes.
-// Variants 2 and 3 keep each frame's messages in shared memory: one frame per
-// block of nbldpc::kResidentThreads threads, no message slots in the workspace.
+// Variants 2 and 3 keep each frame's messages in shared memory: blocks of
+// nbldpc::kResidentThreads threads (1, 2 or 4 frame slots), no message slots in
+// the workspace.
 int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan* out) {
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -161,9 +162,9 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
   const bool resident = kv >= 2;
   const int threads = resident ? nbldpc::kResidentThreads : kThreads;
   if (fpb < 1 || threads % fpb) return NBLDPC_ERR_ARG;
-  if (resident && (fpb != 1 || km != 1 || kq < 16)) return NBLDPC_ERR_UNSUPPORTED;
+  if (resident && km != 1) return NBLDPC_ERR_UNSUPPORTED;
   const int nthr = threads / fpb;
-  if (nthr < 32) return NBLDPC_ERR_UNSUPPORTED;
+  if (nthr < 32 || nthr % 32) return NBLDPC_ERR_UNSUPPORTED;
   Plan pl{};
   pl.fpb = fpb;
   pl.threads = threads;
@@ -200,8 +201,9 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
 
 // Variant when nothing better is known: the one measured fastest for the
 // benchmark codes on GB300 (GF(16), GF(32): layout 1; GF(64): layout 1 with
-// the messages in shared memory; otherwise layout 0).
-int default_variant(int q) { return q == 64 ? 3 : (q >= 16 && q <= 32) ? 1 : 0; }
+// the messages in shared memory; GF(4): layout 0 with the messages in shared
+// memory; otherwise layout 0).
+int default_variant(int q) { return q == 64 ? 3 : q == 4 ? 2 : (q >= 16 && q <= 32) ? 1 : 0; }
 
 // Frame slots per block when nothing better is known: enough threads per slot
 // for the checks and variable nodes of one frame, at least one warp.
@@ -466,10 +468,10 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   e = cudaMemcpy(c->blob_dev, blob.data(), o, cudaMemcpyHostToDevice);
   int st = cuda_status(e);
   if (st == NBLDPC_OK) {
-    // the resident-message form takes one frame per block and must fit shared memory;
-    // otherwise the same layout with the messages in the workspace
+    // the resident-message form (384-thread blocks of 1, 2 or 4 frames) must fit shared
+    // memory; otherwise the same layout with the messages in the workspace
     const int v = default_variant(q), fpb = default_fpb(c);
-    st = (v >= 2 && fpb == 1) ? configure(c, v, fpb) : NBLDPC_ERR_UNSUPPORTED;
+    st = v >= 2 ? configure(c, v, fpb > 4 ? 4 : fpb) : NBLDPC_ERR_UNSUPPORTED;
     if (st == NBLDPC_ERR_UNSUPPORTED) st = configure(c, v & 1, fpb);
   }
   if (st == NBLDPC_OK) {

@@ -268,7 +268,7 @@ def test_every_variant_and_frames_per_block(name, shape):
             tried += 1
             resident += v >= 2
     assert tried >= 2
-    assert resident == (2 if code.q >= 16 else 0)
+    assert resident >= 2            # both layouts with messages in shared memory, one frame per block at least
 
 
 def test_autotune_picks_a_valid_pair_and_keeps_results():
