@@ -69,13 +69,13 @@ def test_every_field_order(q, n, dv, dc):
         assert_same(got, want, f"q={q} early={early}")
 
 
-def irregular_code(q, seed):
-    """Rows of degree 2..9, columns of degree 1..4, random coefficients."""
+def irregular_code(q, seed, dmax=9):
+    """Rows of degree 2..dmax, columns of degree 1..4, random coefficients."""
     rng = np.random.default_rng(seed)
     n, m = 70, 30
     h = np.zeros((m, n), np.int64)
     for r in range(m):
-        d = int(rng.integers(2, 10))
+        d = int(rng.integers(2, dmax + 1))
         cols = rng.choice(n, d, replace=False)
         h[r, cols] = rng.integers(1, q, d)
     for c in range(n):
@@ -95,6 +95,30 @@ def test_irregular_code(q):
         got = gpu_decode(code, g, 7, early)
         want = oracle.decode(code, g, 7, early, threads=THREADS)
         assert_same(got, want, f"irregular q={q}")
+
+
+def test_irregular_gf4_code_in_the_register_form():
+    """Rows of degree 2..8: every check-node pass of a q = 4 code of check degree <= 8 runs in the
+    register form (one lane per check) whatever each row's degree; the same frames through the
+    all-field kernel of a mixed batch take the group form.  Both equal the oracle."""
+    code = irregular_code(4, 43, dmax=8)          # row degrees 2..8
+    assert np.diff(code.row_ptr).max() <= 8 and np.diff(code.row_ptr).min() == 2
+    rng = np.random.default_rng(45)
+    g = rng.integers(0, 40, (40, code.n, 4)).astype(np.uint8)
+    g[np.arange(40)[:, None], np.arange(code.n)[None, :], rng.integers(0, 4, (40, code.n))] = 0
+    dec = binding.Decoder.from_code(code)
+    gd = torch.as_tensor(g).cuda()
+    for v in (0, 1, 2, 3):
+        dec.set_tuning(v, 1)
+        for early in (0, 1):
+            got = [t.cpu().numpy() for t in dec.decode(gd, 7, early)]
+            assert_same(got, oracle.decode(code, g, 7, early, threads=THREADS), f"variant {v} early={early}")
+    jobs, keep = _batch_jobs([(code, g, 7, 1)])
+    ws = torch.empty(binding.nbldpc_decode_batch_workspace_size(jobs), dtype=torch.uint8, device="cuda")
+    binding.nbldpc_decode_batch(jobs, ws)
+    torch.cuda.synchronize()
+    _, _, sym, its, ok = keep[0]
+    assert_same([sym.cpu().numpy(), its.cpu().numpy(), ok.cpu().numpy()], oracle.decode(code, g, 7, 1), "batch")
 
 
 # --------------------------------------------------------------- adversarial inputs
