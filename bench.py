@@ -352,10 +352,33 @@ def alu_peaks(peak_meas, dev):
                   f"(x 2 u16 ops) x {sms} SMs x {mhz:.0f} MHz ({mhz_kind} max SM clock)"), issue
 
 
-def roofline_alu(achieved, peak, peak_kind, issue, traffic=None):
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": peak_kind, "peak_issue_bound": issue,
-            "frac_issue_bound": achieved / issue}
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU pool (the measured-peaks file), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def algorithmic_bytes_per_frame(code) -> int:
+    """HBM bytes one frame must move: its reliabilities in, its symbols, iteration count and ok flag out."""
+    return code.n * code.q + code.n + 5
+
+
+def roofline_alu(achieved, peak, peak_kind, issue, traffic=None, hbm_bytes_per_s=None):
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+         "traffic": traffic, "peak_kind": peak_kind, "peak_issue_bound": issue,
+         "frac_issue_bound": achieved / issue}
+    if hbm_bytes_per_s is not None:
+        # the other roof: algorithmic HBM bytes per second against the measured copy bandwidth
+        gbs, kind = hbm_peak_gbs()
+        r["hbm"] = {"achieved": hbm_bytes_per_s / 1e9, "peak": gbs, "unit": "GB/s",
+                    "frac": hbm_bytes_per_s / 1e9 / gbs, "peak_kind": kind}
+    return r
 
 
 def run_peak(args, ws, rank, local):
@@ -471,7 +494,8 @@ def measure_workload(binding, I, name, dev, local, args, peaks, steps, warmup, f
                       "l2": "inputs larger than L2 (no flush)" if pool == 1 else
                             f"each step decodes the next of {pool} distinct {nf}-frame batches "
                             f"({pool * step_bytes / 1e6:.0f} MB of inputs, > L2; no flush)"},
-           "roofline": roofline_alu(achieved, peak, kind, issue, None if bpf is None else bpf * nf),
+           "roofline": roofline_alu(achieved, peak, kind, issue, None if bpf is None else bpf * nf,
+                                    nf * algorithmic_bytes_per_frame(code) / kernel_s),
            "clocks": clk.summary(), "gpu_launches": int(launches),
            "fer": float((sym.to(torch.int64) != cw).any(-1).float().mean()),
            "not_ok": float(1 - ok.float().mean()), "mean_iters": float(its_h.mean()),
@@ -1216,7 +1240,8 @@ def main():
                    "max_iters": mi, "early_stop": bool(es), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"frames sharded over {ws} GPU(s)", "tuning": tuning},
         "roofline": roofline_alu(achieved_gops, peak_gops, peak_kind, issue_gops,
-                                 None if bpf is None else bpf * frames),
+                                 None if bpf is None else bpf * frames,
+                                 frames * algorithmic_bytes_per_frame(code) / kernel_s),
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": e2e,

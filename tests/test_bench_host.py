@@ -195,3 +195,15 @@ def test_small_workloads_rotate_through_more_than_l2():
     assert n > 1 and n * gf4 > bench.L2_BYTES and (n - 1) * gf4 < 2 * bench.L2_BYTES
     assert bench.batch_pool(196608 * 576 * 64) == 1   # the GF(64) step
     assert bench.batch_pool(16384 * 384 * 256) == 1   # GF(256) N=384, 16384 frames
+
+
+def test_hbm_roof_beside_the_alu_roof():
+    """The roofline object also carries the HBM fraction: algorithmic bytes (reliabilities in,
+    outputs out) per second against the copy bandwidth; for the GF(64) step it is tiny, so the ALU
+    roof binds."""
+    code = I.workload_code("gf64_n576_dv2_dc4")
+    assert bench.algorithmic_bytes_per_frame(code) == 576 * 64 + 576 + 5 == 37445
+    r = bench.roofline_alu(40e3, 55e3, "measured", 80e3, None, 196608 * 37445 / 0.7)
+    gbs, _ = bench.hbm_peak_gbs()
+    assert r["hbm"]["unit"] == "GB/s" and r["hbm"]["frac"] == pytest.approx(196608 * 37445 / 0.7 / 1e9 / gbs)
+    assert r["hbm"]["frac"] < 0.01 < r["frac"]
