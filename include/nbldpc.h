@@ -202,9 +202,17 @@ int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev,
  * of a workspace slot (variants 2 and 3: 8-bit messages, minimal schedule,
  * blocks of 384 threads with 1, 2 or 4 frames, and the messages must fit
  * beside the block's other shared data; otherwise NBLDPC_ERR_UNSUPPORTED).
- * The workspace of such a code is 256 bytes; mixed-code batches use the
- * layout bit only.  nbldpc_code_create picks a default variant per field
- * order and a frames-per-block value from the code size;
+ * The workspace of such a code is 256 bytes.  Bit 2 (variants 4 and 5) prunes
+ * the check-node convolutions: C(x) = min_y max(A(y), B(x ^ y)) equals the
+ * minimum over the y with A(y) <= T for any T >= max_x C(x) (any other y gives
+ * a maximum above C(x)), and likewise with A and B exchanged, so each
+ * convolution folds in only the entries of one side below a bound it finds in
+ * a few phases; the outputs are the same bit for bit.  Bit 2 needs a layout of
+ * 32-lane groups (both layouts of GF(128) and GF(256), layout 0 of GF(64)),
+ * 8-bit messages and the minimal schedule, and excludes bit 1 (otherwise
+ * NBLDPC_ERR_UNSUPPORTED).  Mixed-code batches use the layout bit, and bit 2
+ * for GF(128) and GF(256) codes.  nbldpc_code_create picks a default variant
+ * per field order and a frames-per-block value from the code size;
  * nbldpc_code_autotune measures every valid pair on the caller's frames and
  * keeps the fastest.
  */
@@ -216,10 +224,10 @@ typedef struct nbldpc_tune_result {
 
 int nbldpc_code_get_tuning(const nbldpc_code *code, int *variant, int *frames_per_block);
 
-/* Set the tuning by hand (variant 0..3, frames_per_block 1, 2, 4 or 8); NBLDPC_ERR_UNSUPPORTED if
+/* Set the tuning by hand (variant 0..7, frames_per_block 1, 2, 4 or 8); NBLDPC_ERR_UNSUPPORTED if
  * that pair does not fit the device or the code.  Not concurrent with any other call on the same
  * handle (a decode reads the tuning).  Switching a code to 16-bit messages or to the Table 1
- * schedule drops bit 1 of its variant. */
+ * schedule keeps bit 0 of its variant only. */
 int nbldpc_code_set_tuning(nbldpc_code *code, int variant, int frames_per_block);
 
 /* Device workspace nbldpc_code_autotune needs for `frames` tuning frames. */
@@ -236,6 +244,19 @@ int nbldpc_code_autotune_workspace_size(const nbldpc_code *code, int frames, siz
 int nbldpc_code_autotune(nbldpc_code *code, const uint8_t *gamma_dev, int frames, int max_iters,
                          void *workspace_dev, size_t workspace_bytes, void *cuda_stream,
                          nbldpc_tune_result *results, int max_results, int *n_results);
+
+/*
+ * ---- Work counter --------------------------------------------------------------
+ * With a counter set, every later decode of the code (single-code, batch job,
+ * host-buffer and non-allocating decodes; not the autotuner's) adds to
+ * *counter_dev, by device atomics in stream order, the number of pairs (x, y)
+ * whose max(A(y), B(x ^ y)) its check-node convolutions evaluated: q^2 per
+ * dense convolution, q per entry folded in by a pruned one.  The caller owns the
+ * 8-byte-aligned device counter and clears it; NULL (the default) stops the
+ * count.  Counting adds one atomic per frame and check group; leave it off
+ * when timing.  Not concurrent with any other call on the same handle.
+ */
+int nbldpc_code_set_work_counter(nbldpc_code *code, unsigned long long *counter_dev);
 
 /*
  * ---- Message width ---------------------------------------------------------

@@ -31,7 +31,7 @@ EXPORTED = ("nbldpc_code_create", "nbldpc_code_destroy", "nbldpc_code_info",
             "nbldpc_decode_host", "nbldpc_decode_batch_workspace_size", "nbldpc_decode_batch",
             "nbldpc_code_get_tuning", "nbldpc_code_set_tuning", "nbldpc_code_autotune_workspace_size",
             "nbldpc_code_autotune", "nbldpc_code_set_message_bits", "nbldpc_code_get_message_bits",
-            "nbldpc_code_set_cnp_schedule", "nbldpc_code_get_cnp_schedule",
+            "nbldpc_code_set_cnp_schedule", "nbldpc_code_get_cnp_schedule", "nbldpc_code_set_work_counter",
             "nbldpc_fftspa_workspace_size", "nbldpc_fftspa_decode",
             "nbldpc_fftspa_decode_host_workspace_size", "nbldpc_fftspa_decode_host",
             "nbldpc_server_create", "nbldpc_server_create_custom", "nbldpc_server_submit", "nbldpc_server_poll",
@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
             L.nbldpc_code_get_message_bits.argtypes = [vp, ip]
             L.nbldpc_code_set_cnp_schedule.argtypes = [vp, ctypes.c_int]
             L.nbldpc_code_get_cnp_schedule.argtypes = [vp, ip]
+            L.nbldpc_code_set_work_counter.argtypes = [vp, vp]
             L.nbldpc_fftspa_workspace_size.argtypes = [vp, ctypes.c_int, ctypes.POINTER(sz)]
             L.nbldpc_fftspa_decode.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                                vp, sz, vp]
@@ -356,6 +357,15 @@ def nbldpc_code_set_message_bits(handle: int, bits: int) -> None:
 
 def nbldpc_code_set_cnp_schedule(handle: int, schedule: int) -> None:
     _check(lib().nbldpc_code_set_cnp_schedule(handle, int(schedule)), "nbldpc_code_set_cnp_schedule")
+
+
+def nbldpc_code_set_work_counter(handle: int, counter) -> None:
+    """counter: a torch int64 CUDA tensor of one element (the decodes add to it), or None (off)."""
+    ptr = None
+    if counter is not None:
+        assert counter.is_cuda and counter.dtype == torch.int64 and counter.numel() >= 1
+        ptr = counter.data_ptr()
+    _check(lib().nbldpc_code_set_work_counter(handle, ptr), "nbldpc_code_set_work_counter")
 
 
 def nbldpc_code_get_cnp_schedule(handle: int) -> int:

@@ -56,7 +56,8 @@ struct nbldpc_code {
   int device = 0;
   unsigned char* blob_dev = nullptr;
   nbldpc::CodeBlob off{};
-  int variant = 0;                     // layout variant used by every decode of this code
+  int variant = 0;                     // tuning variant used by every decode of this code
+  unsigned long long* work_counter = nullptr;   // device counter of visited convolution pairs (optional)
   int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
   int cnp_schedule = NBLDPC_CNP_MINIMAL;   // check-node convolutions: 3(d-2) or Table 1's 3d-4
   nbldpc_host::Plan plan{};            // single-code launch shape (fpb chosen by default or by the autotuner)

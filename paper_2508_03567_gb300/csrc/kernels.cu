@@ -13,8 +13,19 @@
 
 namespace nbldpc {
 
+// pruned-convolution kernel of one layout, if that layout has 32-lane groups
+// (a template, so that the layouts without them are never instantiated)
+template <int Q> const void* pruned_kernel(int layout) {
+  if constexpr (Geo<Q, 0>::G == 32)
+    if (layout == 0) return reinterpret_cast<const void*>(&mma_decode_kernel<Q, 0, 1, false, false, true>);
+  if constexpr (Geo<Q, 1>::G == 32)
+    if (layout == 1) return reinterpret_cast<const void*>(&mma_decode_kernel<Q, 1, 1, false, false, true>);
+  return nullptr;
+}
+
 // Address of the decode kernel for variant v (bit 0: layout; bit 1: messages
-// resident in shared memory), mb-byte messages and the check-node schedule t1
+// resident in shared memory; bit 2: pruned convolutions, layouts of 32-lane
+// groups only, not with bit 1), mb-byte messages and the check-node schedule t1
 // (1: Table 1's 3 d_c - 4 convolutions, 8-bit messages only) of this unit's
 // field order; null when there is none.
 const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1) {
@@ -22,6 +33,10 @@ const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1) {
   (void)v;
   return (mb == 1 && !t1) ? reinterpret_cast<const void*>(&mma_decode_kernel<0, -1, 1>) : nullptr;
 #else
+  if (v & 4) {
+    if (mb != 1 || t1 || (v & 2)) return nullptr;
+    return pruned_kernel<NBLDPC_KQ>(v & 1);
+  }
   if (v >= 2) {
     if (mb != 1 || t1) return nullptr;
     return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, false, true>)

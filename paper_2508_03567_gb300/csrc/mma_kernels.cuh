@@ -266,6 +266,144 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
   for (int r = 0; r < g::OPL; ++r) C[ln.c_off + r * g::DN] = (uint16_t)vmin2(acc[r], acc[r] >> 16);
 }
 
+// ---------------------------------------------------------------- pruned convolution
+// The same C = A (*) B, visiting only the y that can decide a minimum.  For any
+// bound T >= max_x C(x), a y with A(y) > T gives max(A(y), B(x ^ y)) > C(x) for
+// every x, so C(x) = min over {y : A(y) <= T} of max(A(y), B(x ^ y)), and the
+// same holds with the roles of A and B exchanged (C is symmetric in them).
+// T is found in phases: the entries of the chosen side with value <= hi are
+// folded in, M = max_x of the partial result is an upper bound of max_x C(x)
+// (a partial minimum is never below the full one), and the phases stop as soon
+// as M <= hi; otherwise hi moves towards M.  The result is C exactly, with no
+// approximation; the work is the number of entries folded in, about
+// 17 of 256 for the GF(256) decoder's vectors instead of 256.
+//
+// One group of 32 lanes (one warp, so every branch below is warp-uniform);
+// lane L owns x = L * OPL + k (k < OPL), kept as OPL/2 packed pairs.  For
+// y = L' * OPL + i, x ^ y = (L ^ L') * OPL + (k ^ i): one aligned vector load of
+// block L ^ L' of the other side, and a permutation inside the block that
+// depends only on i, which the unrolled loop over i makes static.
+// tprev: prediction of max_x C(x) (the previous convolution's maximum); it
+// picks the side with fewer entries below it and the first phase's bound.
+// Returns max_x C(x); with folded non-null, adds the number of entries folded in
+// (each entry is q pairs (x, y)).  Inputs and output must not alias.
+#ifndef NBLDPC_PRUNE_BACK
+#define NBLDPC_PRUNE_BACK 4          // first phase: hi = tprev - NBLDPC_PRUNE_BACK
+#endif
+#ifndef NBLDPC_PRUNE_UNROLL
+#define NBLDPC_PRUNE_UNROLL 2        // entries folded in per loop step
+#endif
+#ifndef NBLDPC_PRUNE_FMA
+#define NBLDPC_PRUNE_FMA 0           // eighths of the maxima on the FMA pipe
+#endif
+#ifndef NBLDPC_PRUNE_PHASES
+#define NBLDPC_PRUNE_PHASES 6        // after this many phases hi jumps to M
+#endif
+template <int NW> __device__ __forceinline__ void load_words(const uint32_t* p, uint32_t (&w)[NW]) {
+  if constexpr (NW == 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else if constexpr (NW == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    w[0] = v.x; w[1] = v.y;
+  } else {
+    w[0] = p[0];
+  }
+}
+
+template <class g>
+__device__ __forceinline__ int pr_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
+                                       uint16_t* __restrict__ C, int lane, int tprev, int* folded) {
+  constexpr int OPL = g::Q / 32, NW = OPL / 2;
+  static_assert(g::G == 32 && OPL >= 2 && NW <= 4, "one warp per convolution");
+  uint32_t a[NW], b[NW];
+  load_words<NW>(A + lane * NW, a);
+  load_words<NW>(B + lane * NW, b);
+  // side: fewer entries <= tprev.  Per 16-bit half, 0x8000 + t - v has bit 15
+  // set exactly when v <= t (values and t below 2^15: no borrow between halves)
+  const uint32_t kt = 0x80008000u + (uint32_t)tprev * 0x10001u;
+  int ca = 0, cb = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    ca += __popc((kt - a[w]) & 0x80008000u);
+    cb += __popc((kt - b[w]) & 0x80008000u);
+  }
+  ca = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)ca);
+  cb = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)cb);
+  const bool swap = cb < ca;
+  const uint32_t* V = swap ? A : B;
+  uint32_t u[NW];
+  int left[OPL];                       // entry values still to fold in (0x10000 once folded)
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    u[w] = swap ? b[w] : a[w];
+    left[2 * w] = (int)(u[w] & 0xFFFFu);
+    left[2 * w + 1] = (int)(u[w] >> 16);
+  }
+  uint32_t acc[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) acc[w] = 0xFFFFFFFFu;
+  int hi = max(tprev - NBLDPC_PRUNE_BACK, 0), M = 0;
+  for (int phase = 1;; ++phase) {
+    unsigned bal[OPL];
+#pragma unroll
+    for (int i = 0; i < OPL; ++i) {
+      const bool p = left[i] <= hi;
+      bal[i] = __ballot_sync(0xFFFFFFFFu, p);
+      if (p) left[i] = 0x10000;
+    }
+#pragma unroll
+    for (int i = 0; i < OPL; ++i) {
+      unsigned m = bal[i];
+      while (m) {
+        // NBLDPC_PRUNE_UNROLL entries per step (a repeated entry changes no minimum)
+        int lp[NBLDPC_PRUNE_UNROLL];
+        lp[0] = __ffs(m) - 1;
+        m &= m - 1;
+#pragma unroll
+        for (int k = 1; k < NBLDPC_PRUNE_UNROLL; ++k) {
+          lp[k] = m ? __ffs(m) - 1 : lp[0];
+          m &= m - 1;
+        }
+        uint32_t uy[NBLDPC_PRUNE_UNROLL], v[NBLDPC_PRUNE_UNROLL][NW];
+#pragma unroll
+        for (int k = 0; k < NBLDPC_PRUNE_UNROLL; ++k) {
+          uy[k] = __byte_perm(__shfl_sync(0xFFFFFFFFu, u[i >> 1], lp[k]), 0, (i & 1) ? 0x3232 : 0x1010);
+          load_words<NW>(V + (lane ^ lp[k]) * NW, v[k]);
+        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+#pragma unroll
+          for (int k = 0; k < NBLDPC_PRUNE_UNROLL; ++k) {
+            uint32_t t = v[k][w ^ (i >> 1)];
+            if (i & 1) t = __byte_perm(t, 0, 0x1032);
+            acc[w] = vmin2(acc[w], (w * NBLDPC_PRUNE_UNROLL + k) * 8 < NBLDPC_PRUNE_FMA * NW * NBLDPC_PRUNE_UNROLL
+                                       ? vmax2_fma(t, uy[k]) : vmax2(t, uy[k]));
+          }
+      }
+    }
+    uint32_t mx = acc[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) mx = vmax2(mx, acc[w]);
+    M = (int)__reduce_max_sync(0xFFFFFFFFu, max(mx & 0xFFFFu, mx >> 16));
+    if (M <= hi || hi >= 0xFFFF) break;                     // (the second: every entry folded in)
+    if (M == 0xFFFF) hi = 2 * hi + 8;                       // nothing folded in yet
+    else if (phase >= NBLDPC_PRUNE_PHASES) hi = M;
+    else hi = min(M, max(hi + 2, (hi + M + 1) >> 1));
+  }
+  if (folded) {               // folded entries carry 0x10000
+    int f = 0;
+#pragma unroll
+    for (int i = 0; i < OPL; ++i) f += left[i] >> 16;
+    *folded += (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)f);
+  }
+  uint32_t* c32 = reinterpret_cast<uint32_t*>(C) + lane * NW;
+  if constexpr (NW == 4) *reinterpret_cast<uint4*>(c32) = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+  else if constexpr (NW == 2) *reinterpret_cast<uint2*>(c32) = make_uint2(acc[0], acc[1]);
+  else c32[0] = acc[0];
+  return M;
+}
+
 // ---------------------------------------------------------------- parameters
 struct CodeBlob {           // offsets (bytes) into the code blob
   int exp2, log, row_ptr, edge_col, edge_lh, edge_lhi, vn_ptr, vn_edge, bytes;
@@ -283,11 +421,12 @@ struct JobDesc {
   int32_t* out_iters;         // [frames]
   uint8_t* out_ok;            // [frames]
   int q, n, m, dmax;
-  int variant;                // layout variant (0 or 1)
+  int variant;                // bit 0: layout; bit 2: pruned convolutions (q >= 128, mixed-code kernel)
   int key16;                  // (255 * (max column degree + 1) + 1) * q <= 65536: 16-bit argmin keys
   int group_bytes;            // per-group shared scratch for this code
   int frames, max_iters, early_stop;
   int item_begin;             // index of this job's first frame in the launch's work list
+  unsigned long long* work;   // optional: adds the (x, y) pairs the convolutions visit (null: no count)
 };
 
 constexpr int kMaxJobs = 32;
@@ -419,8 +558,10 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
 // description, chat[n] the decisions, scratch the per-group buffers; X is the
 // slot's message area ([nnz][q] bytes).
 // REG4: q = 4 codes take the register form of the check-node pass (single-field
-// kernels; the all-field kernel keeps the group form).
-template <class g, int MB, bool T1, bool REG4 = true>
+// kernels; the all-field kernel keeps the group form).  PR: the check-node
+// convolutions are pruned (pr_conv; 32-lane groups, 8-bit messages, minimal
+// schedule).
+template <class g, int MB, bool T1, bool REG4 = true, bool PR = false>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
@@ -428,6 +569,10 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   constexpr int RS = Q * MB;                 // bytes of one message row
   constexpr bool kScatter = scatter_perm<Q>(MB);
   static_assert(MB == 1 || MB == 2, "message bytes");
+  static_assert(!PR || (g::G == 32 && MB == 1 && !T1), "pruned convolutions: 32-lane groups, 8-bit, minimal");
+  // pairs (x, y) the convolutions visit in this frame (counted when job.work is set)
+  const bool counting = job.work != nullptr;
+  unsigned long long work = 0;
   const uint8_t* exp2 = sblob + job.off.exp2;        // x^(i mod (q-1)), i < 2(q-1)
   const uint8_t* glog = sblob + job.off.log;         // log_x(v), v >= 1
   const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.row_ptr);
@@ -623,6 +768,19 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         Pv[y] = (uint16_t)__byte_perm(w[k >> 2], 0, 0x4440 | (k & 3));
       }
     };
+    // predictions of max_x C(x), one per kind of convolution (F, B, beta): each
+    // kind's maxima follow their own distribution
+    int tpred[3] = {24, 24, 24};
+    auto conv = [&](const uint32_t* A, const uint32_t* B, uint16_t* C, int kind) {
+      if constexpr (PR) {
+        int folded = 0;
+        tpred[kind] = pr_conv<g>(A, B, C, gl, tpred[kind], counting ? &folded : nullptr);
+        if (counting && gl == 0) work += (unsigned long long)folded * Q;
+      } else {
+        mm_conv<g, MB == 1>(A, B, C, cl, gmask);
+        if (counting && gl == 0) work += (unsigned long long)Q * Q;
+      }
+    };
     auto cnp = [&](bool first) {
       for (int r = grp; r < job.m; r += ngroups) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
@@ -697,13 +855,14 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j
         int fprev = 0;                                     // vector index of F_{j-1}
         for (int j = 1; j <= d - 2; ++j) {
-          mm_conv<g, MB == 1>(vec(fprev), vec(j), vec16(vF + j), cl, gmask);
+          conv(vec(fprev), vec(j), vec16(vF + j), 0);
           group_sync<g::G>(gmask);
           fprev = vF + j;
         }
         depermute(vec16(fprev), e0 + d - 1);               // beta_{d-1} from F_{d-2}
         if constexpr (T1) {          // Table 1 schedule: F_{d-1} into the scratch vector, unused
           mm_conv<g, MB == 1>(vec(fprev), vec(d - 1), vec16(vR), cl, gmask);
+          if (counting && gl == 0) work += (unsigned long long)Q * Q;
           group_sync<g::G>(gmask);
         }
         // backward: B_{d-1} = P_{d-1}; beta_j from F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j
@@ -711,18 +870,21 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
         int pp = 0;
         for (int j = d - 2; j >= 1; --j) {
           const int fj = (j == 1) ? 0 : vF + j - 1;
-          mm_conv<g, MB == 1>(vec(fj), vec(bcur), vec16(vR), cl, gmask);
+          conv(vec(fj), vec(bcur), vec16(vR), 2);
           group_sync<g::G>(gmask);
           depermute(vec16(vR), e0 + j);
           const int bn = vB + pp;
-          mm_conv<g, MB == 1>(vec(bcur), vec(j), vec16(bn), cl, gmask);
+          conv(vec(bcur), vec(j), vec16(bn), 1);
           group_sync<g::G>(gmask);
           bcur = bn;
           pp ^= 1;
         }
         depermute(vec16(bcur), e0);                        // beta_0 from B_1
         if constexpr (T1)            // Table 1 schedule: B_0 into the scratch vector, unused
+        {
           mm_conv<g, MB == 1>(vec(bcur), vec(0), vec16(vR), cl, gmask);
+          if (counting && gl == 0) work += (unsigned long long)Q * Q;
+        }
         group_sync<g::G>(gmask);
       }
     };
@@ -754,6 +916,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       };
       for (int r = stid; r < job.m; r += nthr) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
+        if (counting && d > 2) work += 16ull * 3 * (d - 2);
         uint32_t P[kRegDeg][2], F[kRegDeg][2];
 #pragma unroll
         for (int j = 0; j < kRegDeg; ++j) {
@@ -824,6 +987,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       }
     }
     for (int i = stid; i < job.n; i += nthr) job.out_sym[(size_t)frame * job.n + i] = chat[i];
+    if (counting && work) atomicAdd(job.work, work);
     if (stid == 0) {
       job.out_iters[frame] = iters;
       job.out_ok[frame] = ok ? 1 : 0;
@@ -848,14 +1012,20 @@ template <int QSEL, int VSEL> struct MinBlocks {
                          : (QSEL == 64 ? (VSEL == 1 ? 3 : NBLDPC_MINB_64) : 4);
 };
 
-// VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job).
-template <int Q, int VSEL, int MB, bool T1 = false>
+// VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job,
+// and for q >= 128 with or without pruned convolutions, bit 2 of the job's variant).
+template <int Q, int VSEL, int MB, bool T1 = false, bool PR = false>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                                uint8_t* chat, unsigned char* scratch, int stid, int nthr,
                                                int bar_id) {
   if constexpr (VSEL >= 0) {
-    decode_frame<Geo<Q, VSEL>, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
-  } else if (job.variant == 0) {
+    decode_frame<Geo<Q, VSEL>, MB, T1, true, PR>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+  } else if (Q >= 128 && (job.variant & 4)) {
+    if constexpr (Q >= 128) {
+      if (job.variant & 1) decode_frame<Geo<Q, 1>, MB, T1, false, true>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      else decode_frame<Geo<Q, 0>, MB, T1, false, true>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    }
+  } else if ((job.variant & 1) == 0) {
     decode_frame<Geo<Q, 0>, MB, T1, false>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else {
     decode_frame<Geo<Q, 1>, MB, T1, false>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
@@ -866,10 +1036,13 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
 // T1: the Table 1 check-node schedule (3 d_c - 4 convolutions; single-field kernels only).
 // XS: the frames' messages stay in shared memory (8-bit messages, single-field
 // kernels; kResidentThreads threads, 1, 2 or 4 frame slots per block).
-template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false>
+// PR: pruned check-node convolutions (single-field kernels whose layout has
+// 32-lane groups; 8-bit messages, minimal schedule).
+template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false, bool PR = false>
 __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : MinBlocks<QSEL, VSEL>::v)
     mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   static_assert(!XS || (QSEL >= 2 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, one field");
+  static_assert(!PR || (QSEL >= 2 && MB == 1 && !T1), "pruned convolutions: 8-bit, minimal schedule, one field");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x / p.fpb;
   const int slot = threadIdx.x / nthr, stid = threadIdx.x % nthr;
@@ -900,7 +1073,7 @@ __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : MinBlock
       slot_sync(bar_id, nthr);
     }
     if constexpr (QSEL != 0) {
-      decode_variant<QSEL, VSEL, MB, T1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      decode_variant<QSEL, VSEL, MB, T1, PR>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
     } else {
       switch (job.q) {
         case 2: decode_variant<2, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;

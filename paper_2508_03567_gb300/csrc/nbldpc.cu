@@ -69,7 +69,8 @@ namespace {
 int kmode(const nbldpc_code* c) { return c->mb == 2 ? 2 : (c->cnp_schedule == NBLDPC_CNP_TABLE1 ? 3 : 1); }
 
 // kernel compiled for one field order, variant (bit 0: layout; bit 1: messages
-// resident in shared memory) and kernel mode, or for every field order (q = 0, mode 1)
+// resident in shared memory; bit 2: pruned convolutions) and kernel mode, or for
+// every field order (q = 0, mode 1)
 const void* kernel_for(int q, int v, int km) {
   const int mb = km == 2 ? 2 : 1, t1 = km == 3 ? 1 : 0;
   switch (q) {
@@ -118,12 +119,13 @@ int group_bytes(int q, int dmax, int mb) {
 
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
-bool g_attr_done[64][65] = {};
+bool g_attr_done[64][81] = {};
 
-// per field order: 3 kernel modes x 2 layouts, then the 2 resident-message kernels
+// per field order: 3 kernel modes x 2 layouts, the 2 resident-message kernels,
+// then the 2 pruned-convolution kernels
 int kernel_slot(int q, int v, int km) {
   if (q == 0) return 0;
-  return 1 + 8 * (nbldpc::ilog2(q) - 1) + (v >= 2 ? 6 + (v & 1) : 2 * (km - 1) + (v & 1));
+  return 1 + 10 * (nbldpc::ilog2(q) - 1) + ((v & 4) ? 8 + (v & 1) : (v & 2) ? 6 + (v & 1) : 2 * (km - 1) + (v & 1));
 }
 
 int prepare_kernel(int q, int v, int km, int dev, int smem_optin) {
@@ -159,7 +161,7 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return NBLDPC_ERR_CUDA;
-  const bool resident = kv >= 2;
+  const bool resident = kv >= 0 && (kv & 2);
   const int threads = resident ? nbldpc::kResidentThreads : kThreads;
   if (fpb < 1 || threads % fpb) return NBLDPC_ERR_ARG;
   if (resident && km != 1) return NBLDPC_ERR_UNSUPPORTED;
@@ -202,8 +204,8 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
 // Variant when nothing better is known: the one measured fastest for the
 // benchmark codes on GB300 (GF(16), GF(32): layout 1; GF(64): layout 1 with
 // the messages in shared memory; GF(4): layout 0 with the messages in shared
-// memory; otherwise layout 0).
-int default_variant(int q) { return q == 64 ? 3 : q == 4 ? 2 : (q >= 16 && q <= 32) ? 1 : 0; }
+// memory; GF(128), GF(256): pruned convolutions, layout 0; otherwise layout 0).
+int default_variant(int q) { return q >= 128 ? 4 : q == 64 ? 3 : q == 4 ? 2 : (q >= 16 && q <= 32) ? 1 : 0; }
 
 // Frame slots per block when nothing better is known: enough threads per slot
 // for the checks and variable nodes of one frame, at least one warp.
@@ -228,7 +230,7 @@ int configure(nbldpc_code* c, int variant, int fpb) {
 size_t decode_ws_bytes(const nbldpc_code* c, int frames) { return ws_bytes(c->plan, frames); }
 
 nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop,
-                         uint8_t* sym, int32_t* iters, uint8_t* ok, int item_begin) {
+                         uint8_t* sym, int32_t* iters, uint8_t* ok, int item_begin, bool count = true) {
   nbldpc::JobDesc j{};
   j.blob = c->blob_dev;
   j.off = c->off;
@@ -240,7 +242,8 @@ nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames,
   j.n = c->n;
   j.m = c->m;
   j.dmax = c->dmax;
-  j.variant = c->variant & 1;          // layout (a mixed-code kernel keeps messages in the workspace)
+  j.variant = c->variant & 5;          // layout and pruning (a mixed-code kernel keeps messages in the workspace)
+  j.work = count ? c->work_counter : nullptr;
   j.key16 = (255 * (c->vmax + 1) + 1) * c->q <= 65536 ? 1 : 0;
   j.group_bytes = group_bytes(c->q, c->dmax, c->mb);
   j.frames = frames;
@@ -272,10 +275,10 @@ int launch_plan(const void* kernel, const Plan& pl, nbldpc::LaunchParams& lp, in
 }
 
 int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters, int early_stop, uint8_t* sym,
-           int32_t* iters, uint8_t* ok, void* ws, cudaStream_t st) {
+           int32_t* iters, uint8_t* ok, void* ws, cudaStream_t st, bool count = true) {
   if (frames == 0) return NBLDPC_OK;
   nbldpc::LaunchParams lp{};
-  lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0);
+  lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0, count);
   lp.njobs = 1;
   lp.total_items = frames;
   return launch_plan(kernel_for(c->q, c->variant, kmode(c)), c->plan, lp, grid_for(c->plan, frames), ws,
@@ -471,7 +474,7 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
     // the resident-message form (384-thread blocks of 1, 2 or 4 frames) must fit shared
     // memory; otherwise the same layout with the messages in the workspace
     const int v = default_variant(q), fpb = default_fpb(c);
-    st = v >= 2 ? configure(c, v, fpb > 4 ? 4 : fpb) : NBLDPC_ERR_UNSUPPORTED;
+    st = v >= 2 ? configure(c, v, (v & 2) && fpb > 4 ? 4 : fpb) : NBLDPC_ERR_UNSUPPORTED;
     if (st == NBLDPC_ERR_UNSUPPORTED) st = configure(c, v & 1, fpb);
   }
   if (st == NBLDPC_OK) {
@@ -513,7 +516,7 @@ int nbldpc_code_get_tuning(const nbldpc_code* c, int* variant, int* frames_per_b
 }
 
 int nbldpc_code_set_tuning(nbldpc_code* c, int variant, int frames_per_block) {
-  if (!c || variant < 0 || variant > 3 || frames_per_block < 1 || frames_per_block > 8 ||
+  if (!c || variant < 0 || variant > 7 || frames_per_block < 1 || frames_per_block > 8 ||
       (frames_per_block & (frames_per_block - 1)))
     return NBLDPC_ERR_ARG;
   const int st = check_device(c);
@@ -556,6 +559,12 @@ int nbldpc_code_set_cnp_schedule(nbldpc_code* c, int schedule) {
 int nbldpc_code_get_cnp_schedule(const nbldpc_code* c, int* schedule) {
   if (!c || !schedule) return NBLDPC_ERR_ARG;
   *schedule = c->cnp_schedule;
+  return NBLDPC_OK;
+}
+
+int nbldpc_code_set_work_counter(nbldpc_code* c, unsigned long long* counter_dev) {
+  if (!c || (counter_dev && !aligned(counter_dev, 8))) return NBLDPC_ERR_ARG;
+  c->work_counter = counter_dev;
   return NBLDPC_OK;
 }
 
@@ -645,7 +654,7 @@ static size_t tune_outputs(const nbldpc_code* c, int frames) {
 int nbldpc_code_autotune_workspace_size(const nbldpc_code* c, int frames, size_t* bytes) {
   if (!c || !bytes || frames < 1) return NBLDPC_ERR_ARG;
   size_t mx = 0;
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < 8; ++v)
     for (int fpb = 1; fpb <= 8; fpb *= 2) {
       Plan pl{};
       const CodeNeeds need = needs_of(c, v, c->mb);
@@ -681,14 +690,14 @@ int nbldpc_code_autotune(nbldpc_code* c, const uint8_t* gamma_dev, int frames, i
   int best_v = v_old, best_f = f_old, count = 0;
   float best = 3.4e38f;
   st = NBLDPC_OK;
-  for (int v = 0; v < 4 && st == NBLDPC_OK; ++v)
+  for (int v = 0; v < 8 && st == NBLDPC_OK; ++v)
     for (int fpb = 1; fpb <= 8 && st == NBLDPC_OK; fpb *= 2) {
       if (configure(c, v, fpb) != NBLDPC_OK) continue;
       // one untimed decode, then one timed decode with fixed iterations
-      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s);
+      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s, false);
       if (st != NBLDPC_OK) break;
       if (cudaEventRecord(e0, s) != cudaSuccess) { st = NBLDPC_ERR_CUDA; break; }
-      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s);
+      st = launch(c, gamma_dev, frames, max_iters, 0, sym, its, okb, dws, s, false);
       if (st != NBLDPC_OK) break;
       float ms = 0.f;
       if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

@@ -278,8 +278,10 @@ def test_every_variant_and_frames_per_block(name, shape):
     want = oracle.decode(code, g, 8, 1, threads=THREADS)
     dec = binding.Decoder.from_code(code)
     gd = torch.as_tensor(g).cuda()
-    tried, resident = 0, 0
-    for v in (0, 1, 2, 3):             # bit 1: messages resident in shared memory (q >= 16, one frame per block)
+    tried, resident, pruned = 0, 0, 0
+    # bit 1: messages resident in shared memory (q >= 16, one frame per block);
+    # bit 2: pruned convolutions (layouts of 32-lane groups: GF(64) layout 0, GF(128), GF(256))
+    for v in range(8):
         for fpb in (1, 2, 4, 8):
             try:
                 dec.set_tuning(v, fpb)
@@ -290,9 +292,12 @@ def test_every_variant_and_frames_per_block(name, shape):
             got = [t.cpu().numpy() for t in dec.decode(gd, 8, 1)]
             assert_same(got, want, f"{name} variant {v} fpb {fpb}")
             tried += 1
-            resident += v >= 2
+            resident += (v & 2) != 0
+            pruned += (v & 4) != 0
     assert tried >= 2
     assert resident >= 2            # both layouts with messages in shared memory, one frame per block at least
+    if code.q >= 64:
+        assert pruned >= 4          # every frames-per-block count of at least one pruned layout
 
 
 def test_autotune_picks_a_valid_pair_and_keeps_results():
