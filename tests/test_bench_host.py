@@ -207,3 +207,13 @@ def test_hbm_roof_beside_the_alu_roof():
     gbs, _ = bench.hbm_peak_gbs()
     assert r["hbm"]["unit"] == "GB/s" and r["hbm"]["frac"] == pytest.approx(196608 * 37445 / 0.7 / 1e9 / gbs)
     assert r["hbm"]["frac"] < 0.01 < r["frac"]
+
+
+def test_pruned_work_is_reported_beside_the_dense_count():
+    """The roofline counts the pairs the kernel visited; a pruned decode also reports the rate its
+    time gives the paper's dense count (which may exceed the peak), a dense one does not."""
+    r = bench.roofline_alu(30e3, 55e3, "measured", 80e3, dense=120e3)
+    assert r["frac"] == pytest.approx(30 / 55) and r["work"].startswith("executed")
+    assert r["dense_equivalent"]["frac"] == pytest.approx(120 / 55)
+    r = bench.roofline_alu(30e3, 55e3, "measured", 80e3, dense=30e3)
+    assert "dense_equivalent" not in r and "work" not in r
