@@ -236,7 +236,8 @@ int nbldpc_code_autotune_workspace_size(const nbldpc_code *code, int frames, siz
 /*
  * Time a fixed-iteration decode (max_iters >= 1, no early stop) of the
  * caller's `frames` frames gamma_dev for every valid (variant,
- * frames-per-block) pair, keep the fastest, and report each measurement in
+ * frames-per-block) pair (the fastest of three timed decodes after an untimed
+ * one), keep the fastest pair, and report each measurement in
  * results[0 .. min(max_results, *n_results)).  Synchronous: returns after the
  * measurements (it waits on `cuda_stream`).  Not thread safe with respect to
  * other calls on the same handle.

@@ -1007,6 +1007,12 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 #ifndef NBLDPC_MINB_WIDE
 #define NBLDPC_MINB_WIDE 2
 #endif
+// The pruned kernels fit 80 registers without spilling: three 256-thread blocks
+// per SM hide more of their shuffle and shared-memory latency (GF(256) (2,6)
+// N=384: 119.8 ms at two blocks, 103.8 at three, 106.5 at four).
+#ifndef NBLDPC_MINB_PRUNE
+#define NBLDPC_MINB_PRUNE 3
+#endif
 template <int QSEL, int VSEL> struct MinBlocks {
   static constexpr int v = QSEL == 0 ? 2 : QSEL >= 128 ? NBLDPC_MINB_WIDE
                          : (QSEL == 64 ? (VSEL == 1 ? 3 : NBLDPC_MINB_64) : 4);
@@ -1039,7 +1045,7 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
 // PR: pruned check-node convolutions (single-field kernels whose layout has
 // 32-lane groups; 8-bit messages, minimal schedule).
 template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false, bool PR = false>
-__global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : MinBlocks<QSEL, VSEL>::v)
+__global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : PR ? NBLDPC_MINB_PRUNE : MinBlocks<QSEL, VSEL>::v)
     mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   static_assert(!XS || (QSEL >= 2 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, one field");
   static_assert(!PR || (QSEL >= 2 && MB == 1 && !T1), "pruned convolutions: 8-bit, minimal schedule, one field");
