@@ -285,6 +285,9 @@ __device__ __forceinline__ void mm_conv(const uint32_t* __restrict__ A, const ui
 // depends only on i, which the unrolled loop over i makes static.
 // tprev: prediction of max_x C(x) (the previous convolution's maximum); it
 // picks the side with fewer entries below it and the first phase's bound.
+// SW (q >= 128, else null): a scratch vector for the other side with the two
+// halves of every word exchanged, so that the odd i read their block without
+// permuting it.
 // Returns max_x C(x); with folded non-null, adds the number of entries folded in
 // (each entry is q pairs (x, y)).  Inputs and output must not alias.
 #ifndef NBLDPC_PRUNE_BACK
@@ -313,7 +316,8 @@ template <int NW> __device__ __forceinline__ void load_words(const uint32_t* p, 
 
 template <class g>
 __device__ __forceinline__ int pr_conv(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
-                                       uint16_t* __restrict__ C, int lane, int tprev, int* folded) {
+                                       uint16_t* __restrict__ C, uint32_t* __restrict__ SW, int lane, int tprev,
+                                       int* folded) {
   constexpr int OPL = g::Q / 32, NW = OPL / 2;
   static_assert(g::G == 32 && OPL >= 2 && NW <= 4, "one warp per convolution");
   uint32_t a[NW], b[NW];
@@ -339,6 +343,15 @@ __device__ __forceinline__ int pr_conv(const uint32_t* __restrict__ A, const uin
     u[w] = swap ? b[w] : a[w];
     left[2 * w] = (int)(u[w] & 0xFFFFu);
     left[2 * w + 1] = (int)(u[w] >> 16);
+  }
+  constexpr bool kSw = g::Q >= 128;
+  if constexpr (kSw) {
+    uint32_t t[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t[w] = __byte_perm(swap ? a[w] : b[w], 0, 0x1032);
+    if constexpr (NW == 4) *reinterpret_cast<uint4*>(SW + lane * NW) = make_uint4(t[0], t[1], t[2], t[3]);
+    else *reinterpret_cast<uint2*>(SW + lane * NW) = make_uint2(t[0], t[1]);
+    __syncwarp();
   }
   uint32_t acc[NW];
 #pragma unroll
@@ -369,14 +382,14 @@ __device__ __forceinline__ int pr_conv(const uint32_t* __restrict__ A, const uin
 #pragma unroll
         for (int k = 0; k < NBLDPC_PRUNE_UNROLL; ++k) {
           uy[k] = __byte_perm(__shfl_sync(0xFFFFFFFFu, u[i >> 1], lp[k]), 0, (i & 1) ? 0x3232 : 0x1010);
-          load_words<NW>(V + (lane ^ lp[k]) * NW, v[k]);
+          load_words<NW>(((i & 1) && kSw ? SW : V) + (lane ^ lp[k]) * NW, v[k]);
         }
 #pragma unroll
         for (int w = 0; w < NW; ++w)
 #pragma unroll
           for (int k = 0; k < NBLDPC_PRUNE_UNROLL; ++k) {
             uint32_t t = v[k][w ^ (i >> 1)];
-            if (i & 1) t = __byte_perm(t, 0, 0x1032);
+            if ((i & 1) && !kSw) t = __byte_perm(t, 0, 0x1032);
             acc[w] = vmin2(acc[w], (w * NBLDPC_PRUNE_UNROLL + k) * 8 < NBLDPC_PRUNE_FMA * NW * NBLDPC_PRUNE_UNROLL
                                        ? vmax2_fma(t, uy[k]) : vmax2(t, uy[k]));
           }
@@ -462,9 +475,11 @@ template <int Q> __host__ __device__ constexpr bool scatter_perm(int mb) {
 
 // per-group shared scratch: the d incoming rows (q symbols of mb bytes each;
 // not with the scatter permutation) and 2*dmax+1 16-bit vectors: P_0..P_{d-1},
-// F_1..F_{d-2}, two B vectors and the middle beta R
+// F_1..F_{d-2}, two B vectors and the middle beta R; q >= 128: one more, the
+// pruned convolution's half-swapped copy of its second operand
 template <int Q> __host__ __device__ constexpr int group_scratch_bytes(int dmax, int mb = 1) {
-  return (scatter_perm<Q>(mb) ? 0 : ((dmax * Q * mb + 15) / 16) * 16) + (2 * dmax + 1) * vec_bytes<Q>();
+  return (scatter_perm<Q>(mb) ? 0 : ((dmax * Q * mb + 15) / 16) * 16) +
+         (2 * dmax + 1 + (Q >= 128 ? 1 : 0)) * vec_bytes<Q>();
 }
 
 // named barrier over the threads of one frame slot (ids 1..fpb)
@@ -774,7 +789,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     auto conv = [&](const uint32_t* A, const uint32_t* B, uint16_t* C, int kind) {
       if constexpr (PR) {
         int folded = 0;
-        tpred[kind] = pr_conv<g>(A, B, C, gl, tpred[kind], counting ? &folded : nullptr);
+        tpred[kind] = pr_conv<g>(A, B, C, Q >= 128 ? vec(2 * job.dmax + 1) : nullptr, gl, tpred[kind],
+                                 counting ? &folded : nullptr);
         if (counting && gl == 0) work += (unsigned long long)folded * Q;
       } else {
         mm_conv<g, MB == 1>(A, B, C, cl, gmask);
