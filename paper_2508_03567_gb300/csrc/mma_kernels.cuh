@@ -567,6 +567,18 @@ template <int G> __device__ __forceinline__ unsigned group_mask(int lane) {
   return (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
+// ---------------------------------------------------------------- q = 4 in registers
+// C(x) = min_y max(A(y), B(x ^ y)) on 4-symbol vectors held as two words of
+// 16-bit values, (v0, v1) and (v2, v3): B ^ 1 swaps the halves of each word,
+// B ^ 2 swaps the words.
+__device__ __forceinline__ uint2 conv4(uint2 a, uint2 b) {
+  const uint32_t a0 = __byte_perm(a.x, 0, 0x1010), a1 = __byte_perm(a.x, 0, 0x3232);
+  const uint32_t a2 = __byte_perm(a.y, 0, 0x1010), a3 = __byte_perm(a.y, 0, 0x3232);
+  const uint32_t s0 = __byte_perm(b.x, 0, 0x1032), s1 = __byte_perm(b.y, 0, 0x1032);
+  return make_uint2(vmin2(vmin2(vmax2(a0, b.x), vmax2(a1, s0)), vmin2(vmax2(a2, b.y), vmax2(a3, s1))),
+                    vmin2(vmin2(vmax2(a0, b.y), vmax2(a1, s1)), vmin2(vmax2(a2, b.x), vmax2(a3, s0))));
+}
+
 // ---------------------------------------------------------------- one frame
 // Decodes frame `frame` of `job` with the nthr threads of one frame slot
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
@@ -609,6 +621,8 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   const int vgrp = stid / VG, nvgroups = nthr / VG;
   const int vgl = stid % VG;
   const unsigned vmask = group_mask<VG>(lane);
+  constexpr bool kGammaRegs = Q <= 16 && MB == 1;
+  uint32_t gcache[kGammaRegs ? VW : 1];
 
   // lane constants for the gather permutation (staged rows): logarithms of the
   // symbols this lane gathers, packed 8 bits per symbol; the zero symbol, which
@@ -688,12 +702,25 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
       }
     };
 
+    // q <= 16 with every variable node in one pass of the slot's lanes: each lane
+    // keeps its node's gamma words in registers from the first pass on (the later
+    // passes then start without a global-memory load)
+    const bool gamma_regs = kGammaRegs && job.n <= nvgroups;
     auto vnp = [&](bool first, bool want_alpha) {
       // symbol values of this lane's packed words: (a, a + 1), a = vgl * VBPL + 2 i
       const uint32_t vsym0 = (uint32_t)(vgl * VBPL) * 0x10001u + 0x10000u;
       for (int vn = vgrp; vn < job.n; vn += nvgroups) {
         uint32_t S[VW];
-        load_pairs<VBPL>(gam + (size_t)vn * Q + vgl * VBPL, S);
+        if (gamma_regs && !first) {
+#pragma unroll
+          for (int i = 0; i < VW; ++i) S[i] = gcache[i];
+        } else {
+          load_pairs<VBPL>(gam + (size_t)vn * Q + vgl * VBPL, S);
+          if (gamma_regs) {
+#pragma unroll
+            for (int i = 0; i < VW; ++i) gcache[i] = S[i];
+          }
+        }
         const int k0 = vn_ptr[vn], k1 = vn_ptr[vn + 1];
         if (!first) {
           for (int k = k0; k < k1; ++k) {
@@ -912,30 +939,27 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     // pass has no memory round trip between its steps (at q = 4 the group form
     // is a chain of short shared-memory dependencies).
     constexpr int kRegDeg = 8;
-    // C(x) = min_y max(A(y), B(x ^ y)): B ^ 1 swaps the halves of each word, B ^ 2 swaps the words
-    auto conv4 = [](const uint32_t (&a)[2], const uint32_t (&b)[2], uint32_t (&c)[2]) {
-      const uint32_t a0 = __byte_perm(a[0], 0, 0x1010), a1 = __byte_perm(a[0], 0, 0x3232);
-      const uint32_t a2 = __byte_perm(a[1], 0, 0x1010), a3 = __byte_perm(a[1], 0, 0x3232);
-      const uint32_t s0 = __byte_perm(b[0], 0, 0x1032), s1 = __byte_perm(b[1], 0, 0x1032);
-      c[0] = vmin2(vmin2(vmax2(a0, b[0]), vmax2(a1, s0)), vmin2(vmax2(a2, b[1]), vmax2(a3, s1)));
-      c[1] = vmin2(vmin2(vmax2(a0, b[1]), vmax2(a1, s1)), vmin2(vmax2(a2, b[0]), vmax2(a3, s0)));
-    };
     auto cnp_regs4 = [&](bool first) {
       // beta_e(a) = R(h a): byte a of the row from the 16-bit value R(i), i = h a, of the words R
-      auto store_beta = [&](int e, const uint32_t (&R)[2]) {
+      auto store_beta = [&](int e, uint2 R) {
         const int lh = edge_lh[e];
         const int i1 = exp2[lh], i2 = exp2[lh + 1], i3 = i1 ^ i2;
         const uint32_t sel = (uint32_t)((((i1 >> 1) << 2) | ((i1 & 1) << 1)) << 4) |
                              (uint32_t)((((i2 >> 1) << 2) | ((i2 & 1) << 1)) << 8) |
                              (uint32_t)((((i3 >> 1) << 2) | ((i3 & 1) << 1)) << 12);
-        *reinterpret_cast<uint32_t*>(X + (size_t)e * 4) = __byte_perm(R[0], R[1], sel);
+        *reinterpret_cast<uint32_t*>(X + (size_t)e * 4) = __byte_perm(R.x, R.y, sel);
       };
       for (int r = stid; r < job.m; r += nthr) {
         const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
         if (counting && d > 2) work += 16ull * 3 * (d - 2);
-        uint32_t P[kRegDeg][2], F[kRegDeg][2];
+        // The last P and F are tracked as the loops run (Plast = P_{d-1}, Flast =
+        // F_{d-2}): picking them out afterwards by "j == d - 1" turns into an indexed
+        // access, which sends the arrays to local memory.
+        uint2 P[kRegDeg], F[kRegDeg], Plast = make_uint2(0u, 0u);
 #pragma unroll
         for (int j = 0; j < kRegDeg; ++j) {
+          P[j] = make_uint2(0u, 0u);
+          F[j] = make_uint2(0u, 0u);
           if (j < d) {
             // P_j(y) = alpha_j(h^-1 y): (alpha(0), alpha(h^-1)), (alpha(h^-1 2), alpha(h^-1 3))
             const int e = e0 + j;
@@ -943,33 +967,28 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
                                        : *reinterpret_cast<const uint32_t*>(X + (size_t)e * 4);
             const int lhinv = edge_lhi[e];
             const uint32_t s1 = exp2[lhinv], s2 = exp2[lhinv + 1], s3 = s1 ^ s2;
-            P[j][0] = __byte_perm(row, 0, 0x4040u | (s1 << 8));
-            P[j][1] = __byte_perm(row, 0, 0x4040u | s2 | (s3 << 8));
+            P[j].x = __byte_perm(row, 0, 0x4040u | (s1 << 8));
+            P[j].y = __byte_perm(row, 0, 0x4040u | s2 | (s3 << 8));
+            Plast = P[j];
           }
         }
         // forward: F_0 = P_0, F_j = F_{j-1} (*) P_j; beta_{d-1} = F_{d-2}
-        F[0][0] = P[0][0];
-        F[0][1] = P[0][1];
+        F[0] = P[0];
+        uint2 Flast = F[0];
 #pragma unroll
         for (int j = 1; j < kRegDeg - 1; ++j)
-          if (j <= d - 2) conv4(F[j - 1], P[j], F[j]);
-#pragma unroll
-        for (int j = 0; j < kRegDeg - 1; ++j)
-          if (j == d - 2) store_beta(e0 + d - 1, F[j]);
+          if (j <= d - 2) {
+            F[j] = conv4(F[j - 1], P[j]);
+            Flast = F[j];
+          }
+        store_beta(e0 + d - 1, Flast);
         // backward: B_{d-1} = P_{d-1}; beta_j = F_{j-1} (*) B_{j+1}; B_j = B_{j+1} (*) P_j; beta_0 = B_1
-        uint32_t Bc[2] = {0u, 0u};
-#pragma unroll
-        for (int j = 1; j < kRegDeg; ++j)
-          if (j == d - 1) { Bc[0] = P[j][0]; Bc[1] = P[j][1]; }
+        uint2 Bc = Plast;
 #pragma unroll
         for (int j = kRegDeg - 2; j >= 1; --j) {
           if (j <= d - 2) {
-            uint32_t R[2], Bn[2];
-            conv4(F[j - 1], Bc, R);
-            store_beta(e0 + j, R);
-            conv4(Bc, P[j], Bn);
-            Bc[0] = Bn[0];
-            Bc[1] = Bn[1];
+            store_beta(e0 + j, conv4(F[j - 1], Bc));
+            Bc = conv4(Bc, P[j]);
           }
         }
         store_beta(e0, Bc);
