@@ -204,10 +204,10 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
 // Variant when nothing better is known: the one measured fastest for the
 // benchmark codes on GB300 (GF(16), GF(32): layout 1; GF(64): layout 1 with
 // the messages in shared memory; GF(4): layout 0 with the messages in shared
-// memory; GF(256): pruned convolutions, layout 0 (2.3x the dense kernel at
-// (2,6) N=384; at GF(128) (2,4) N=256 the pruned form is 8 % slower); otherwise
+// memory; GF(128), GF(256): pruned convolutions, layout 0 (GF(256) (2,6) N=384:
+// 2.8x the dense kernel; GF(128) (2,4) N=256: 35.6 against 41.1 ms); otherwise
 // layout 0).
-int default_variant(int q) { return q == 256 ? 4 : q == 64 ? 3 : q == 4 ? 2 : (q >= 16 && q <= 32) ? 1 : 0; }
+int default_variant(int q) { return q >= 128 ? 4 : q == 64 ? 3 : q == 4 ? 2 : (q >= 16 && q <= 32) ? 1 : 0; }
 
 // Frame slots per block when nothing better is known: enough threads per slot
 // for the checks and variable nodes of one frame, at least one warp.
