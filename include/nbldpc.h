@@ -200,8 +200,12 @@ int nbldpc_decode_batch(const nbldpc_job *jobs, int n_jobs, void *workspace_dev,
  * min-max work of one convolution is split between the lanes of a group and
  * their registers); bit 1 keeps each frame's messages in shared memory instead
  * of a workspace slot (variants 2 and 3: 8-bit messages, minimal schedule,
- * blocks of 384 threads with 1, 2 or 4 frames, and the messages must fit
- * beside the block's other shared data; otherwise NBLDPC_ERR_UNSUPPORTED).
+ * blocks of 384 threads with 1, 2 or 4 frames or of 256 threads with 8, and
+ * the messages must fit beside the block's other shared data; otherwise
+ * NBLDPC_ERR_UNSUPPORTED).  With one warp per frame (8 frames per block, or
+ * any single-code launch whose frame slots are 32 threads) a GF(4) code of at
+ * most 32 checks of degree <= 4 and columns of degree <= 2 is decoded by that
+ * warp alone, with no block-wide barrier.
  * The workspace of such a code is 256 bytes.  Bit 2 (variants 4 and 5) prunes
  * the check-node convolutions: C(x) = min_y max(A(y), B(x ^ y)) equals the
  * minimum over the y with A(y) <= T for any T >= max_x C(x) (any other y gives

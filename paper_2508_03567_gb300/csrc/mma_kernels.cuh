@@ -433,7 +433,7 @@ struct JobDesc {
   uint8_t* out_sym;           // [frames][n]
   int32_t* out_iters;         // [frames]
   uint8_t* out_ok;            // [frames]
-  int q, n, m, dmax;
+  int q, n, m, dmax, vmax;    // field order, columns, rows, largest row and column degree
   int variant;                // bit 0: layout; bit 2: pruned convolutions (q >= 128, mixed-code kernel)
   int key16;                  // (255 * (max column degree + 1) + 1) * q <= 65536: 16-bit argmin keys
   int group_bytes;            // per-group shared scratch for this code
@@ -579,6 +579,182 @@ __device__ __forceinline__ uint2 conv4(uint2 a, uint2 b) {
                     vmin2(vmin2(vmax2(a0, b.y), vmax2(a1, s1)), vmin2(vmax2(a2, b.x), vmax2(a3, s0))));
 }
 
+
+// ---------------------------------------------------------------- q = 4, one warp per frame
+// A frame of a small GF(4) code (at most 32 checks of degree <= kW4Deg, columns
+// of degree <= 2) decoded by one warp with no block barrier: lane r owns check r
+// and keeps its edges' alpha and beta rows (4 bytes each) in registers; the
+// permutation and de-permutation byte selectors and the GF(4) products of its
+// edges are set up once per frame; beta goes to the slot's message area (one
+// word per edge) only for the variable-node step of the other edge's owner.
+// Each edge's owner computes its variable node's sum, decision and next alpha,
+// so every variable node is handled by the lanes of its (one or two) edges.
+// The arithmetic is that of the other forms (Alg. 2): the same convolutions,
+// the same min-normalization, saturation at 255 and lowest-symbol argmin.
+// Returns false, having done nothing, when the code is outside these limits.
+constexpr int kW4Deg = 4;
+__device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame, uint8_t* X,
+                                                   const unsigned char* sblob, int lane) {
+  if (job.m > 32 || job.dmax > kW4Deg || job.vmax > 2) return false;
+  const uint8_t* exp2 = sblob + job.off.exp2;
+  const uint8_t* glog = sblob + job.off.log;
+  const uint16_t* row_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.row_ptr);
+  const uint16_t* edge_col = reinterpret_cast<const uint16_t*>(sblob + job.off.edge_col);
+  const uint8_t* edge_lh = sblob + job.off.edge_lh;
+  const uint8_t* edge_lhi = sblob + job.off.edge_lhi;
+  const uint16_t* vn_ptr = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_ptr);
+  const uint16_t* vn_edge = reinterpret_cast<const uint16_t*>(sblob + job.off.vn_edge);
+  const uint8_t* gam = job.gamma + (size_t)frame * job.n * 4;
+  const bool mine = lane < job.m;
+  const int e0 = mine ? row_ptr[lane] : 0, d = mine ? row_ptr[lane + 1] - e0 : 0;
+  // per edge j < d: gamma row of its column, selectors, products, the other edge (-1: none)
+  uint32_t gr[kW4Deg], psel[kW4Deg], bsel[kW4Deg], mt[kW4Deg], al[kW4Deg], be[kW4Deg];
+  int oe[kW4Deg], col[kW4Deg];
+  bool first_owner[kW4Deg];
+#pragma unroll
+  for (int j = 0; j < kW4Deg; ++j) {
+    gr[j] = psel[j] = bsel[j] = mt[j] = al[j] = be[j] = 0u;
+    oe[j] = -1;
+    col[j] = 0;
+    first_owner[j] = false;
+    if (j < d) {
+      const int e = e0 + j, c = edge_col[e];
+      col[j] = c;
+      gr[j] = *reinterpret_cast<const uint32_t*>(gam + (size_t)c * 4);
+      // P_j(y) = alpha_j(h^-1 y) as the 16-bit pairs (P(0), P(1)), (P(2), P(3))
+      const int lhinv = edge_lhi[e];
+      const uint32_t s1 = exp2[lhinv], s2 = exp2[lhinv + 1], s3 = s1 ^ s2;
+      psel[j] = (0x4040u | (s1 << 8)) | ((0x4040u | s2 | (s3 << 8)) << 16);
+      // beta_j(a) = R(h a): byte a from the 16-bit value R(h a) of the pairs R
+      const int lh = edge_lh[e];
+      const int i1 = exp2[lh], i2 = exp2[lh + 1], i3 = i1 ^ i2;
+      bsel[j] = (uint32_t)((((i1 >> 1) << 2) | ((i1 & 1) << 1)) << 4) |
+                (uint32_t)((((i2 >> 1) << 2) | ((i2 & 1) << 1)) << 8) |
+                (uint32_t)((((i3 >> 1) << 2) | ((i3 & 1) << 1)) << 12);
+      // h c for c = 0..3, two bits each (syndrome)
+      mt[j] = (uint32_t)exp2[lh] << 2 | (uint32_t)exp2[glog[2] + lh] << 4 | (uint32_t)exp2[glog[3] + lh] << 6;
+      const int k0 = vn_ptr[c], k1 = vn_ptr[c + 1];
+      first_owner[j] = vn_edge[k0] == e;
+      for (int k = k0; k < k1; ++k)
+        if (vn_edge[k] != e) oe[j] = vn_edge[k];
+      al[j] = gr[j];                             // alpha^(0) = gamma
+    }
+  }
+  const bool counting = job.work != nullptr;
+  unsigned long long work = 0;
+  // decisions from the sums S = gamma + the incoming betas (lowest symbol on ties), and the syndrome
+  uint32_t cw = 0;                               // decisions of the lane's edges, two bits each
+  auto decide = [&](int j, uint32_t s0, uint32_t s1) {
+    const uint32_t kw = vmin2(s0 * 4u + 0x10000u, s1 * 4u + 0x30002u);
+    const uint32_t key = min(kw & 0xFFFFu, kw >> 16);
+    cw |= (key & 3u) << (2 * j);
+  };
+  auto syndrome_ok = [&]() -> bool {
+    uint32_t sy = 0;
+#pragma unroll
+    for (int j = 0; j < kW4Deg; ++j)
+      if (j < d) sy ^= (mt[j] >> (2 * ((cw >> (2 * j)) & 3u))) & 3u;
+    return __all_sync(0xFFFFFFFFu, sy == 0);
+  };
+  auto unpack = [](uint32_t r, uint32_t& lo, uint32_t& hi) {
+    lo = __byte_perm(r, 0, 0x4140);
+    hi = __byte_perm(r, 0, 0x4342);
+  };
+  // c^(0) = argmin gamma
+#pragma unroll
+  for (int j = 0; j < kW4Deg; ++j)
+    if (j < d) {
+      uint32_t g0, g1;
+      unpack(gr[j], g0, g1);
+      decide(j, g0, g1);
+    }
+  const bool es = job.early_stop != 0;
+  bool ok = (es || job.max_iters == 0) ? syndrome_ok() : false;
+  int iters = 0;
+  if (!(es && ok)) {
+    for (int k = 1; k <= job.max_iters; ++k) {
+      // check-node pass (the register form of one check)
+      if (counting && d > 2) work += 16ull * 3 * (d - 2);
+      uint2 P[kW4Deg], F[kW4Deg], Plast = make_uint2(0u, 0u);
+#pragma unroll
+      for (int j = 0; j < kW4Deg; ++j) {
+        P[j] = make_uint2(0u, 0u);
+        F[j] = make_uint2(0u, 0u);
+        if (j < d) {
+          P[j].x = __byte_perm(al[j], 0, psel[j] & 0xFFFFu);
+          P[j].y = __byte_perm(al[j], 0, psel[j] >> 16);
+          Plast = P[j];
+        }
+      }
+      F[0] = P[0];
+      uint2 Flast = F[0];
+#pragma unroll
+      for (int j = 1; j < kW4Deg - 1; ++j)
+        if (j <= d - 2) {
+          F[j] = conv4(F[j - 1], P[j]);
+          Flast = F[j];
+        }
+      uint2 Bc = Plast;
+      uint2 R[kW4Deg];
+#pragma unroll
+      for (int j = 0; j < kW4Deg; ++j) R[j] = make_uint2(0u, 0u);
+#pragma unroll
+      for (int j = kW4Deg - 2; j >= 1; --j) {
+        if (j <= d - 2) {
+          R[j] = conv4(F[j - 1], Bc);
+          Bc = conv4(Bc, P[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kW4Deg; ++j) {
+        if (j < d) {
+          // beta_0 = B_1, beta_{d-1} = F_{d-2}, else the middle R_j
+          const uint2 r = j == 0 ? Bc : (j == d - 1 ? Flast : R[j]);
+          be[j] = __byte_perm(r.x, r.y, bsel[j]);
+          reinterpret_cast<uint32_t*>(X)[e0 + j] = be[j];
+        }
+      }
+      __syncwarp();
+      // variable-node step of each of the lane's edges: S = gamma + beta_e + beta_other;
+      // alpha_e = min(255, (S - beta_e) - min (S - beta_e))
+      const bool decide_now = es || k == job.max_iters;
+      if (decide_now) cw = 0;
+#pragma unroll
+      for (int j = 0; j < kW4Deg; ++j) {
+        if (j < d) {
+          uint32_t t0, t1, b0, b1;
+          unpack(gr[j], t0, t1);
+          if (oe[j] >= 0) {
+            unpack(reinterpret_cast<const uint32_t*>(X)[oe[j]], b0, b1);
+            t0 += b0;
+            t1 += b1;
+          }
+          if (decide_now) {
+            unpack(be[j], b0, b1);
+            decide(j, t0 + b0, t1 + b1);
+          }
+          const uint32_t mw = vmin2(t0, t1);
+          const uint32_t mm = min(mw & 0xFFFFu, mw >> 16) * 0x10001u;
+          al[j] = __byte_perm(vmin2(t0 - mm, 0x00FF00FFu), vmin2(t1 - mm, 0x00FF00FFu), 0x6420);
+        }
+      }
+      __syncwarp();
+      iters = k;
+      if (decide_now) ok = syndrome_ok();
+      if (es && ok) break;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kW4Deg; ++j)
+    if (j < d && first_owner[j]) job.out_sym[(size_t)frame * job.n + col[j]] = (uint8_t)((cw >> (2 * j)) & 3u);
+  if (lane == 0) {
+    job.out_iters[frame] = iters;
+    job.out_ok[frame] = ok ? 1 : 0;
+  }
+  if (counting && work) atomicAdd(job.work, work);
+  return true;
+}
+
 // ---------------------------------------------------------------- one frame
 // Decodes frame `frame` of `job` with the nthr threads of one frame slot
 // (slot thread index stid, named barrier bar_id).  sblob holds the job's code
@@ -587,8 +763,9 @@ __device__ __forceinline__ uint2 conv4(uint2 a, uint2 b) {
 // REG4: q = 4 codes take the register form of the check-node pass (single-field
 // kernels; the all-field kernel keeps the group form).  PR: the check-node
 // convolutions are pruned (pr_conv; 32-lane groups, 8-bit messages, minimal
-// schedule).
-template <class g, int MB, bool T1, bool REG4 = true, bool PR = false>
+// schedule).  W4: a GF(4) frame slot of one warp may take the one-warp form
+// (decode_frame_warp4; resident-message kernels, which have the registers for it).
+template <class g, int MB, bool T1, bool REG4 = true, bool PR = false, bool W4 = false>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
@@ -597,6 +774,10 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   constexpr bool kScatter = scatter_perm<Q>(MB);
   static_assert(MB == 1 || MB == 2, "message bytes");
   static_assert(!PR || (g::G == 32 && MB == 1 && !T1), "pruned convolutions: 32-lane groups, 8-bit, minimal");
+  if constexpr (Q == 4 && MB == 1 && !T1 && REG4 && W4) {
+    // one warp per frame: a slot of 32 threads
+    if (nthr == 32 && decode_frame_warp4(job, frame, X, sblob, stid)) return;
+  }
   // pairs (x, y) the convolutions visit in this frame (counted when job.work is set)
   const bool counting = job.work != nullptr;
   unsigned long long work = 0;
@@ -1055,12 +1236,12 @@ template <int QSEL, int VSEL> struct MinBlocks {
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job,
 // and for q >= 128 with or without pruned convolutions, bit 2 of the job's variant).
-template <int Q, int VSEL, int MB, bool T1 = false, bool PR = false>
+template <int Q, int VSEL, int MB, bool T1 = false, bool PR = false, bool W4 = false>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                                uint8_t* chat, unsigned char* scratch, int stid, int nthr,
                                                int bar_id) {
   if constexpr (VSEL >= 0) {
-    decode_frame<Geo<Q, VSEL>, MB, T1, true, PR>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, VSEL>, MB, T1, true, PR, W4>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (Q >= 128 && (job.variant & 4)) {
     if constexpr (Q >= 128) {
       if (job.variant & 1) decode_frame<Geo<Q, 1>, MB, T1, false, true>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
@@ -1114,7 +1295,7 @@ __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : PR ? NBL
       slot_sync(bar_id, nthr);
     }
     if constexpr (QSEL != 0) {
-      decode_variant<QSEL, VSEL, MB, T1, PR>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      decode_variant<QSEL, VSEL, MB, T1, PR, XS>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
     } else {
       switch (job.q) {
         case 2: decode_variant<2, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;

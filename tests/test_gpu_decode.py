@@ -485,3 +485,59 @@ def test_eq1_worked_iteration_on_the_gpu():
                 assert_same(got, oracle.decode(code, gamma, iters, 0), f"v{v} fpb{fpb} {iters} it")
             s, i, o = (t.cpu().numpy() for t in dec.decode(gt, 5, 1))
             assert np.all(s == g["decision"][0]) and np.all(i == 1) and np.all(o == 1)
+
+
+# --------------------------------------------------------------- GF(4): one warp per frame
+def small_gf4_code(seed, m=20, n=36, max_row=4, max_col=2):
+    """Rows of degree 2..max_row, columns of degree 1..max_col, at least one column of degree 1 and
+    one of degree max_col: column sockets dealt to rows of drawn degrees (no repeated column)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(10000):
+        col_deg = rng.integers(1, max_col + 1, n)
+        col_deg[0], col_deg[1] = 1, max_col
+        e = int(col_deg.sum())
+        if not 2 * m <= e <= max_row * m:
+            continue
+        row_deg = np.full(m, 2)
+        for r in rng.permutation(np.repeat(np.arange(m), max_row - 2))[: e - 2 * m]:
+            row_deg[r] += 1
+        sockets = rng.permutation(np.repeat(np.arange(n), col_deg))
+        rows = np.repeat(np.arange(m), row_deg)
+        h = np.zeros((m, n), np.int64)
+        if len(set(zip(rows.tolist(), sockets.tolist()))) < e:
+            continue
+        h[rows, sockets] = rng.integers(1, 4, e)
+        return I.code_from_dense(h, 4, I.PRIMITIVE_POLY[4])
+    raise RuntimeError("no code")
+
+
+@pytest.mark.parametrize("shape", ["workload", "degree1_columns", "degree3_columns", "m40"])
+def test_gf4_one_warp_per_frame(shape):
+    """Variants 2 and 3 at 8 frames per block give each GF(4) frame one warp: codes of <= 32 checks
+    of degree <= 4 and columns of degree <= 2 take the one-warp form, others the group or register
+    form in the same 32-thread slot; every output equals the oracle's, with and without early stop,
+    on channel frames and on the adversarial inputs."""
+    if shape == "workload":
+        code = I.workload_code("gf4_n48_dv2_dc4")
+    elif shape == "degree1_columns":
+        code = small_gf4_code(5)
+        assert np.bincount(code.col_idx, minlength=code.n).min() == 1
+    elif shape == "degree3_columns":
+        code = small_gf4_code(6, max_col=3)
+    else:
+        code = small_gf4_code(7, m=40, n=72)
+    rng = np.random.default_rng(11)
+    f, n = 24, code.n
+    gs = [I.make_batch(code, eb, 31 + k, f).gamma.numpy() for k, eb in enumerate((1.0, 3.0))]
+    gs += [np.full((6, n, 4), 9, np.uint8), rng.choice(np.array([0, 255], np.uint8), (6, n, 4)),
+           rng.integers(0, 256, (6, n, 4)).astype(np.uint8), np.zeros((6, n, 4), np.uint8)]
+    dec = binding.Decoder.from_code(code)
+    for v in (2, 3):
+        dec.set_tuning(v, 8)
+        assert dec.tuning() == (v, 8)
+        for g in gs:
+            gd = torch.as_tensor(g).cuda()
+            for mi, early in ((10, 0), (10, 1), (0, 1), (1, 0)):
+                got = [t.cpu().numpy() for t in dec.decode(gd, mi, early)]
+                assert_same(got, oracle.decode(code, g, mi, early, threads=THREADS),
+                            f"{shape} variant {v} max_iters={mi} early={early}")
