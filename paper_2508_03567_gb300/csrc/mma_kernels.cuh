@@ -456,6 +456,7 @@ struct LaunchParams {
   int slot_smem;              // shared bytes per frame slot
   int blob_cap, n_cap;        // largest code blob and N among the jobs
   int xs_off;                 // resident launches: shared-memory offset of the slot's messages
+  int static_items;           // 1: no more items than frame slots; slot s takes item s (no counter)
 };
 
 // Threads of a block whose frame keeps its messages in shared memory (two
@@ -1277,8 +1278,12 @@ __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : PR ? NBL
   uint8_t* X = XS ? base + p.xs_off : p.msg + ((size_t)blockIdx.x * p.fpb + slot) * p.slot_bytes;
   int staged = -1;
 
+  // a launch with no more items than frame slots assigns them statically (the
+  // host then skips the counter reset)
+  int static_item = p.static_items ? (int)blockIdx.x * p.fpb + slot : -1;
   for (;;) {
-    if (stid == 0) ctl[0] = (int)atomicAdd(p.counter, 1u);
+    if (stid == 0) ctl[0] = static_item >= 0 ? static_item : (int)atomicAdd(p.counter, 1u);
+    if (static_item >= 0) static_item = p.total_items;
     slot_sync(bar_id, nthr);
     const int item = ctl[0];
     if (item >= p.total_items) break;

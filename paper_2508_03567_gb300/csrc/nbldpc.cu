@@ -262,7 +262,8 @@ nbldpc::JobDesc job_desc(const nbldpc_code* c, const uint8_t* gamma, int frames,
   return j;
 }
 
-// Queue the counter reset and the persistent kernel (grid blocks) on st.
+// Queue the counter reset (not needed when every frame has its own slot) and the
+// persistent kernel (grid blocks) on st.
 int launch_plan(const void* kernel, const Plan& pl, nbldpc::LaunchParams& lp, int grid, void* counter, uint8_t* msg,
                 cudaStream_t st) {
   if (lp.total_items == 0 || grid < 1) return NBLDPC_OK;
@@ -274,8 +275,13 @@ int launch_plan(const void* kernel, const Plan& pl, nbldpc::LaunchParams& lp, in
   lp.blob_cap = pl.blob_cap;
   lp.n_cap = pl.n_cap;
   lp.xs_off = pl.xs_off;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  // no more frames than frame slots: slot s takes frame s, no counter to reset
+  lp.static_items = (long long)lp.total_items <= (long long)grid * pl.fpb ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  if (!lp.static_items) {
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
+  }
   void* args[] = {&lp};
   e = cudaLaunchKernel(kernel, dim3(grid), dim3(pl.threads), args, (size_t)pl.smem, st);
   if (e != cudaSuccess) return NBLDPC_ERR_CUDA;
