@@ -27,6 +27,10 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct CudaExec {
   int device = 0;
   std::vector<cudaStream_t> streams;
+  // the server's own stream-ordered pool: it keeps up to the budget mapped
+  // between launches (the default pool returns freed memory to the system at
+  // synchronizations, and mapping it again stalled the next launches)
+  cudaMemPool_t pool = nullptr;
   struct Launch {
     cudaEvent_t ev = nullptr;
   };
@@ -39,6 +43,7 @@ struct CudaExec {
       cudaEventDestroy(kv.second.ev);
     }
     for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    if (pool) cudaMemPoolDestroy(pool);
   }
 
   static int shape(const nbldpc_request* r, int* n, int* q) {
@@ -87,7 +92,8 @@ struct CudaExec {
     const size_t wsb = launch_bytes(nullptr, reqs, n, plain);
     total += wsb;
     unsigned char* buf = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&buf), total, st) != cudaSuccess) return NBLDPC_ERR_NOMEM;
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&buf), total, ex->pool, st) != cudaSuccess)
+      return NBLDPC_ERR_NOMEM;
     nbldpc_job jobs[NBLDPC_MAX_BATCH_JOBS];
     size_t ws_cur = ws_off;
     int status = NBLDPC_OK;
@@ -217,6 +223,17 @@ int nbldpc_server_create(size_t budget_bytes, int streams, int max_jobs, int pla
   CudaExec* cx = new (std::nothrow) CudaExec();
   if (!cx) return NBLDPC_ERR_NOMEM;
   if (cudaGetDevice(&cx->device) != cudaSuccess) {
+    delete cx;
+    return NBLDPC_ERR_CUDA;
+  }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = cx->device;
+  uint64_t keep = budget_bytes;
+  if (cudaMemPoolCreate(&cx->pool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(cx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
     delete cx;
     return NBLDPC_ERR_CUDA;
   }
