@@ -133,16 +133,16 @@ def dense_pairs(code, iters):
     return int(np.asarray(iters, np.int64).sum()) * int((3 * np.maximum(d - 2, 0)).sum()) * code.q ** 2
 
 
-@pytest.mark.parametrize("name,variant", [("gf4_n48_dv2_dc4", 2), ("gf4_n48_dv2_dc4", 0),
-                                          ("gf16_n1024_dv2_dc4", 1), ("gf64_n576_dv2_dc4", 3),
-                                          ("gf256_n128_dv2_dc8", 0)])
-def test_work_counter_of_dense_convolutions_is_the_schedule_count(name, variant):
+@pytest.mark.parametrize("name,variant,fpb", [("gf4_n48_dv2_dc4", 2, 1), ("gf4_n48_dv2_dc4", 2, 8),
+                                              ("gf4_n48_dv2_dc4", 0, 1), ("gf16_n1024_dv2_dc4", 1, 1),
+                                              ("gf64_n576_dv2_dc4", 3, 1), ("gf256_n128_dv2_dc8", 0, 1)])
+def test_work_counter_of_dense_convolutions_is_the_schedule_count(name, variant, fpb):
     """Dense convolutions visit q^2 pairs each, 3(d_c - 2) per check and iteration (the GF(4)
-    register form and the group form alike)."""
+    register form, the GF(4) one-warp form at 8 frames per block, and the group form alike)."""
     w = I.WORKLOADS[name]
     code = I.workload_code(name)
     dec = binding.Decoder.from_code(code)
-    dec.set_tuning(variant, 1)
+    dec.set_tuning(variant, fpb)
     g = I.make_batch(code, w["ebn0"][0], 909, 40).gamma.cuda()
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     binding.nbldpc_code_set_work_counter(dec.handle, cnt)
