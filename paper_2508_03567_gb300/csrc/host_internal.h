@@ -57,6 +57,7 @@ struct nbldpc_code {
   unsigned char* blob_dev = nullptr;
   nbldpc::CodeBlob off{};
   int variant = 0;                     // tuning variant used by every decode of this code
+  int dreg = 0;                        // degree of every check when all are equal, else 0
   unsigned long long* work_counter = nullptr;   // device counter of visited convolution pairs (optional)
   int mb = 1;                          // message bytes per symbol (1: 8-bit messages, 2: 16-bit)
   int cnp_schedule = NBLDPC_CNP_MINIMAL;   // check-node convolutions: 3(d-2) or Table 1's 3d-4

@@ -766,7 +766,9 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
 // convolutions are pruned (pr_conv; 32-lane groups, 8-bit messages, minimal
 // schedule).  W4: a GF(4) frame slot of one warp may take the one-warp form
 // (decode_frame_warp4; resident-message kernels, which have the registers for it).
-template <class g, int MB, bool T1, bool REG4 = true, bool PR = false, bool W4 = false>
+// D > 0: every check of the code has degree D (a compile-time loop bound and
+// vector layout; 0: the degrees are read per check).
+template <class g, int MB, bool T1, bool REG4 = true, bool PR = false, bool W4 = false, int D = 0>
 __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                              uint8_t* chat, unsigned char* scratch, int stid, int nthr, int bar_id) {
   constexpr int Q = g::Q;
@@ -825,12 +827,13 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
 
   unsigned char* gs = scratch + (size_t)grp * job.group_bytes;
   uint8_t* stage = gs;                                                   // [dmax][q * MB] bytes (staged rows)
-  unsigned char* vecs = gs + (kScatter ? 0 : ((job.dmax * RS + 15) / 16) * 16);
+  const int dm = D > 0 ? D : job.dmax;
+  unsigned char* vecs = gs + (kScatter ? 0 : ((dm * RS + 15) / 16) * 16);
   auto vec = [&](int i) { return reinterpret_cast<uint32_t*>(vecs + (size_t)i * g::VB); };
   auto vec16 = [&](int i) { return reinterpret_cast<uint16_t*>(vecs + (size_t)i * g::VB); };
   // vectors: P_j = vec(j) (j < dmax), F_j = vec(dmax + j - 1) (1 <= j <= d-2),
   // B ping-pong = vec(2 dmax - 2), vec(2 dmax - 1), R = vec(2 dmax)
-  const int vF = job.dmax - 1, vB = 2 * job.dmax - 2, vR = 2 * job.dmax;
+  const int vF = dm - 1, vB = 2 * dm - 2, vR = 2 * dm;
   const uint8_t* gam = job.gamma + (size_t)frame * job.n * Q;
 
     // ---- variable-node pass (Alg. 2, VNP and hard decision):
@@ -998,7 +1001,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     auto conv = [&](const uint32_t* A, const uint32_t* B, uint16_t* C, int kind) {
       if constexpr (PR) {
         int folded = 0;
-        tpred[kind] = pr_conv<g>(A, B, C, Q >= 128 ? vec(2 * job.dmax + 1) : nullptr, gl, tpred[kind],
+        tpred[kind] = pr_conv<g>(A, B, C, Q >= 128 ? vec(2 * dm + 1) : nullptr, gl, tpred[kind],
                                  counting ? &folded : nullptr);
         if (counting && gl == 0) work += (unsigned long long)folded * Q;
       } else {
@@ -1008,7 +1011,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
     };
     auto cnp = [&](bool first) {
       for (int r = grp; r < job.m; r += ngroups) {
-        const int e0 = row_ptr[r], d = row_ptr[r + 1] - e0;
+        const int e0 = row_ptr[r], d = D > 0 ? D : row_ptr[r + 1] - e0;
         if constexpr (kScatter) {
           for (int c = gl; c < d * CH; c += g::G) scatter_piece(first, e0, c);
         } else {
@@ -1237,12 +1240,12 @@ template <int QSEL, int VSEL> struct MinBlocks {
 
 // VSEL = 0 or 1 compiles one layout variant; VSEL = -1 both (chosen per job,
 // and for q >= 128 with or without pruned convolutions, bit 2 of the job's variant).
-template <int Q, int VSEL, int MB, bool T1 = false, bool PR = false, bool W4 = false>
+template <int Q, int VSEL, int MB, bool T1 = false, bool PR = false, bool W4 = false, int D = 0>
 __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, uint8_t* X, const unsigned char* sblob,
                                                uint8_t* chat, unsigned char* scratch, int stid, int nthr,
                                                int bar_id) {
   if constexpr (VSEL >= 0) {
-    decode_frame<Geo<Q, VSEL>, MB, T1, true, PR, W4>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+    decode_frame<Geo<Q, VSEL>, MB, T1, true, PR, W4, D>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
   } else if (Q >= 128 && (job.variant & 4)) {
     if constexpr (Q >= 128) {
       if (job.variant & 1) decode_frame<Geo<Q, 1>, MB, T1, false, true>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
@@ -1260,8 +1263,9 @@ __device__ __forceinline__ void decode_variant(const JobDesc& job, int frame, ui
 // XS: the frames' messages stay in shared memory (8-bit messages, single-field
 // kernels; kResidentThreads threads, 1, 2 or 4 frame slots per block).
 // PR: pruned check-node convolutions (single-field kernels whose layout has
-// 32-lane groups; 8-bit messages, minimal schedule).
-template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false, bool PR = false>
+// 32-lane groups; 8-bit messages, minimal schedule).  D > 0: every check has
+// degree D (single-field kernels; see decode_frame).
+template <int QSEL, int VSEL, int MB, bool T1 = false, bool XS = false, bool PR = false, int D = 0>
 __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : PR ? NBLDPC_MINB_PRUNE : MinBlocks<QSEL, VSEL>::v)
     mma_decode_kernel(const __grid_constant__ LaunchParams p) {
   static_assert(!XS || (QSEL >= 2 && MB == 1 && !T1), "resident messages: 8-bit, minimal schedule, one field");
@@ -1300,7 +1304,7 @@ __global__ void __launch_bounds__(XS ? kResidentThreads : 256, XS ? 2 : PR ? NBL
       slot_sync(bar_id, nthr);
     }
     if constexpr (QSEL != 0) {
-      decode_variant<QSEL, VSEL, MB, T1, PR, XS>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
+      decode_variant<QSEL, VSEL, MB, T1, PR, XS, D>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id);
     } else {
       switch (job.q) {
         case 2: decode_variant<2, -1, 1>(job, frame, X, sblob, chat, scratch, stid, nthr, bar_id); break;

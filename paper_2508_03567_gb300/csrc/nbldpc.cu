@@ -51,15 +51,15 @@ bool build_field(int q, uint32_t poly, std::vector<uint8_t>& exp2, std::vector<u
 }  // namespace
 
 namespace nbldpc {   // defined in kernels.cu, one translation unit per field order
-const void* kernel_q0(int v, int mb, int t1);
-const void* kernel_q2(int v, int mb, int t1);
-const void* kernel_q4(int v, int mb, int t1);
-const void* kernel_q8(int v, int mb, int t1);
-const void* kernel_q16(int v, int mb, int t1);
-const void* kernel_q32(int v, int mb, int t1);
-const void* kernel_q64(int v, int mb, int t1);
-const void* kernel_q128(int v, int mb, int t1);
-const void* kernel_q256(int v, int mb, int t1);
+const void* kernel_q0(int v, int mb, int t1, int dreg);
+const void* kernel_q2(int v, int mb, int t1, int dreg);
+const void* kernel_q4(int v, int mb, int t1, int dreg);
+const void* kernel_q8(int v, int mb, int t1, int dreg);
+const void* kernel_q16(int v, int mb, int t1, int dreg);
+const void* kernel_q32(int v, int mb, int t1, int dreg);
+const void* kernel_q64(int v, int mb, int t1, int dreg);
+const void* kernel_q128(int v, int mb, int t1, int dreg);
+const void* kernel_q256(int v, int mb, int t1, int dreg);
 }  // namespace nbldpc
 
 namespace {
@@ -69,23 +69,27 @@ namespace {
 int kmode(const nbldpc_code* c) { return c->mb == 2 ? 2 : (c->cnp_schedule == NBLDPC_CNP_TABLE1 ? 3 : 1); }
 
 // kernel compiled for one field order, variant (bit 0: layout; bit 1: messages
-// resident in shared memory; bit 2: pruned convolutions) and kernel mode, or for
-// every field order (q = 0, mode 1)
-const void* kernel_for(int q, int v, int km) {
+// resident in shared memory; bit 2: pruned convolutions), kernel mode and the
+// code's regular check degree (dreg: 0 when the rows differ; a field order may
+// have a kernel for it), or for every field order (q = 0, mode 1)
+const void* kernel_for(int q, int v, int km, int dreg = 0) {
   const int mb = km == 2 ? 2 : 1, t1 = km == 3 ? 1 : 0;
   switch (q) {
-    case 0: return nbldpc::kernel_q0(-1, mb, t1);
-    case 2: return nbldpc::kernel_q2(v, mb, t1);
-    case 4: return nbldpc::kernel_q4(v, mb, t1);
-    case 8: return nbldpc::kernel_q8(v, mb, t1);
-    case 16: return nbldpc::kernel_q16(v, mb, t1);
-    case 32: return nbldpc::kernel_q32(v, mb, t1);
-    case 64: return nbldpc::kernel_q64(v, mb, t1);
-    case 128: return nbldpc::kernel_q128(v, mb, t1);
-    case 256: return nbldpc::kernel_q256(v, mb, t1);
+    case 0: return nbldpc::kernel_q0(-1, mb, t1, 0);
+    case 2: return nbldpc::kernel_q2(v, mb, t1, dreg);
+    case 4: return nbldpc::kernel_q4(v, mb, t1, dreg);
+    case 8: return nbldpc::kernel_q8(v, mb, t1, dreg);
+    case 16: return nbldpc::kernel_q16(v, mb, t1, dreg);
+    case 32: return nbldpc::kernel_q32(v, mb, t1, dreg);
+    case 64: return nbldpc::kernel_q64(v, mb, t1, dreg);
+    case 128: return nbldpc::kernel_q128(v, mb, t1, dreg);
+    case 256: return nbldpc::kernel_q256(v, mb, t1, dreg);
   }
   return nullptr;
 }
+
+// the regular check degree that selects a specialised kernel (see kernel_for), else 0
+int kernel_dreg(int q, int v, int km, int dreg) { return (q == 64 && km == 1 && v >= 2 && v <= 3 && dreg == 4) ? 4 : 0; }
 
 template <int Q> int lanes(int v) { return v ? nbldpc::Geo<Q, 1>::G : nbldpc::Geo<Q, 0>::G; }
 
@@ -119,21 +123,23 @@ int group_bytes(int q, int dmax, int mb) {
 
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
-bool g_attr_done[64][81] = {};
+bool g_attr_done[64][83] = {};
 
 // per field order: 3 kernel modes x 2 layouts, the 2 resident-message kernels,
-// then the 2 pruned-convolution kernels
-int kernel_slot(int q, int v, int km) {
+// then the 2 pruned-convolution kernels; after them the 2 GF(64) resident kernels
+// of check degree 4
+int kernel_slot(int q, int v, int km, int dreg) {
   if (q == 0) return 0;
+  if (kernel_dreg(q, v, km, dreg)) return 81 + (v & 1);
   return 1 + 10 * (nbldpc::ilog2(q) - 1) + ((v & 4) ? 8 + (v & 1) : (v & 2) ? 6 + (v & 1) : 2 * (km - 1) + (v & 1));
 }
 
-int prepare_kernel(int q, int v, int km, int dev, int smem_optin) {
+int prepare_kernel(int q, int v, int km, int dreg, int dev, int smem_optin) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (dev < 0 || dev >= 64) return NBLDPC_ERR_CUDA;
-  const void* k = kernel_for(q, v, km);
+  const void* k = kernel_for(q, v, km, dreg);
   if (!k) return NBLDPC_ERR_UNSUPPORTED;
-  bool& done = g_attr_done[dev][kernel_slot(q, v, km)];
+  bool& done = g_attr_done[dev][kernel_slot(q, v, km, dreg)];
   if (!done) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
       return NBLDPC_ERR_CUDA;
@@ -145,10 +151,12 @@ int prepare_kernel(int q, int v, int km, int dev, int smem_optin) {
 struct CodeNeeds {       // what one code asks of a frame slot
   int q, variant, mb, dmax, blob, n;
   size_t msg;
+  int dreg;              // regular check degree (0: the rows differ)
 };
 
 CodeNeeds needs_of(const nbldpc_code* c, int variant, int mb) {
-  return CodeNeeds{c->q, variant, mb, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q * mb, 256)};
+  return CodeNeeds{c->q, variant, mb, c->dmax, c->off.bytes, c->n, round_up((size_t)c->nnz * c->q * mb, 256),
+                   c->dreg};
 }
 
 // Plan a launch of kernel (kq, kv, kernel mode km) with fpb frame slots per block for a set of codes.
@@ -190,9 +198,10 @@ int make_plan(int kq, int kv, int km, int fpb, const CodeNeeds* cs, int nc, Plan
   }
   pl.smem = fpb * pl.slot_smem;
   if (pl.smem > optin) return NBLDPC_ERR_UNSUPPORTED;
-  int st = prepare_kernel(kq, kv, km, dev, optin);
+  const int dreg = (kq != 0 && nc == 1) ? cs[0].dreg : 0;
+  int st = prepare_kernel(kq, kv, km, dreg, dev, optin);
   if (st != NBLDPC_OK) return st;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv, km), pl.threads, pl.smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm, kernel_for(kq, kv, km, dreg), pl.threads, pl.smem) !=
       cudaSuccess)
     return NBLDPC_ERR_CUDA;
   if (pl.per_sm < 1) return NBLDPC_ERR_UNSUPPORTED;
@@ -296,7 +305,7 @@ int launch(const nbldpc_code* c, const uint8_t* gamma, int frames, int max_iters
   lp.jobs[0] = job_desc(c, gamma, frames, max_iters, early_stop, sym, iters, ok, 0, count);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant, kmode(c)), c->plan, lp, grid_for(c->plan, frames), ws,
+  return launch_plan(kernel_for(c->q, c->variant, kmode(c), c->dreg), c->plan, lp, grid_for(c->plan, frames), ws,
                      reinterpret_cast<uint8_t*>(ws) + 256, st);
 }
 
@@ -349,7 +358,7 @@ int nbldpc_decode_noalloc(const nbldpc_code* c, const uint8_t* gamma_dev, int fr
   lp.jobs[0] = job_desc(c, gamma_dev, frames, max_iters, early_stop, out_sym_dev, out_iters_dev, out_ok_dev, 0);
   lp.njobs = 1;
   lp.total_items = frames;
-  return launch_plan(kernel_for(c->q, c->variant, kmode(c)), pl, lp, grid, scratch,
+  return launch_plan(kernel_for(c->q, c->variant, kmode(c), c->dreg), pl, lp, grid, scratch,
                      reinterpret_cast<uint8_t*>(scratch) + 256,
                      reinterpret_cast<cudaStream_t>(cuda_stream));
 }
@@ -477,6 +486,9 @@ int nbldpc_code_create(int q, uint32_t prim_poly, int n_cols, int n_rows, const 
   c->nnz = nnz;
   c->dmax = dmax;
   c->vmax = vmax;
+  c->dreg = dmax;                      // regular check degree, or 0 when the rows differ
+  for (int r = 0; r < n_rows; ++r)
+    if (row_ptr[r + 1] - row_ptr[r] != dmax) c->dreg = 0;
   c->ntasks = (int)tasks.size() - 1;
   c->poly = prim_poly;
   c->off = off;
