@@ -51,7 +51,7 @@ enum {
   NBLDPC_ERR_CUDA = -4,        /* a CUDA call failed (also reports earlier asynchronous faults) */
   NBLDPC_ERR_NOMEM = -5,       /* device or host allocation failed inside nbldpc_code_create */
   NBLDPC_ERR_TIMEOUT = -6,     /* reserved: a bounded device-side wait expired */
-  NBLDPC_ERR_UNSUPPORTED = -7  /* valid code outside this build's limits (see nbldpc_code_create) */
+  NBLDPC_ERR_UNSUPPORTED = -7  /* valid code outside the library's limits (see nbldpc_code_create) */
 };
 
 /*

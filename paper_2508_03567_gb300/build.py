@@ -75,7 +75,7 @@ def build_library(force: bool = False, verbose: bool = False, jobs: int | None =
         subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp])
         os.replace(tmp, lib)
     finally:
-        # this build's objects (and a half-written library) go, whether it succeeded or not
+        # the objects of this compilation (and a half-written library) go, whether it succeeded or not
         for o in outs + [tmp]:
             if os.path.exists(o):
                 os.remove(o)
