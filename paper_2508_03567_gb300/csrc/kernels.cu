@@ -27,8 +27,8 @@ template <int Q> const void* pruned_kernel(int layout) {
 // resident in shared memory; bit 2: pruned convolutions, layouts of 32-lane
 // groups only, not with bit 1), mb-byte messages and the check-node schedule t1
 // (1: Table 1's 3 d_c - 4 convolutions, 8-bit messages only) of this unit's
-// field order; dreg: the code's check degree when all are equal (GF(64) has
-// resident-message kernels for degree 4), else 0; null when there is none.
+// field order; dreg: the code's check degree when all are equal (GF(4) and
+// GF(64) have resident-message kernels for degree 4), else 0; null when there is none.
 const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1, int dreg) {
   (void)dreg;
 #if NBLDPC_KQ == 0
@@ -41,11 +41,11 @@ const void* NBLDPC_CAT(kernel_q, NBLDPC_KQ)(int v, int mb, int t1, int dreg) {
   }
   if (v >= 2) {
     if (mb != 1 || t1) return nullptr;
-#if NBLDPC_KQ == 64
+#if NBLDPC_KQ == 64 || NBLDPC_KQ == 4
     // every check of degree 4 (the regular (2,4) codes): a compile-time check degree
     if (dreg == 4)
-      return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<64, 1, 1, false, true, false, 4>)
-                     : reinterpret_cast<const void*>(&mma_decode_kernel<64, 0, 1, false, true, false, 4>);
+      return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, false, true, false, 4>)
+                     : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1, false, true, false, 4>);
 #endif
     return (v & 1) ? reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 1, 1, false, true>)
                    : reinterpret_cast<const void*>(&mma_decode_kernel<NBLDPC_KQ, 0, 1, false, true>);

@@ -593,7 +593,9 @@ __device__ __forceinline__ uint2 conv4(uint2 a, uint2 b) {
 // The arithmetic is that of the other forms (Alg. 2): the same convolutions,
 // the same min-normalization, saturation at 255 and lowest-symbol argmin.
 // Returns false, having done nothing, when the code is outside these limits.
+// DW = 4: every check has degree 4 (the per-iteration loops need no degree tests).
 constexpr int kW4Deg = 4;
+template <int DW>
 __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame, uint8_t* X,
                                                    const unsigned char* sblob, int lane) {
   if (job.m > 32 || job.dmax > kW4Deg || job.vmax > 2) return false;
@@ -608,6 +610,8 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
   const uint8_t* gam = job.gamma + (size_t)frame * job.n * 4;
   const bool mine = lane < job.m;
   const int e0 = mine ? row_ptr[lane] : 0, d = mine ? row_ptr[lane + 1] - e0 : 0;
+  // degree of the per-iteration loops: the lanes without a check compute on zeros and store nothing
+  const int dd = DW > 0 ? DW : d;
   // per edge j < d: gamma row of its column, selectors, products, the other edge (-1: none)
   uint32_t gr[kW4Deg], psel[kW4Deg], bsel[kW4Deg], mt[kW4Deg], al[kW4Deg], be[kW4Deg];
   int oe[kW4Deg], col[kW4Deg];
@@ -654,7 +658,7 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
     uint32_t sy = 0;
 #pragma unroll
     for (int j = 0; j < kW4Deg; ++j)
-      if (j < d) sy ^= (mt[j] >> (2 * ((cw >> (2 * j)) & 3u))) & 3u;
+      if (j < d) sy ^= (mt[j] >> (2 * ((cw >> (2 * j)) & 3u))) & 3u;   // (mt is 0 past d)
     return __all_sync(0xFFFFFFFFu, sy == 0);
   };
   auto unpack = [](uint32_t r, uint32_t& lo, uint32_t& hi) {
@@ -681,7 +685,7 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
       for (int j = 0; j < kW4Deg; ++j) {
         P[j] = make_uint2(0u, 0u);
         F[j] = make_uint2(0u, 0u);
-        if (j < d) {
+        if (j < dd) {
           P[j].x = __byte_perm(al[j], 0, psel[j] & 0xFFFFu);
           P[j].y = __byte_perm(al[j], 0, psel[j] >> 16);
           Plast = P[j];
@@ -691,7 +695,7 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
       uint2 Flast = F[0];
 #pragma unroll
       for (int j = 1; j < kW4Deg - 1; ++j)
-        if (j <= d - 2) {
+        if (j <= dd - 2) {
           F[j] = conv4(F[j - 1], P[j]);
           Flast = F[j];
         }
@@ -701,18 +705,18 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
       for (int j = 0; j < kW4Deg; ++j) R[j] = make_uint2(0u, 0u);
 #pragma unroll
       for (int j = kW4Deg - 2; j >= 1; --j) {
-        if (j <= d - 2) {
+        if (j <= dd - 2) {
           R[j] = conv4(F[j - 1], Bc);
           Bc = conv4(Bc, P[j]);
         }
       }
 #pragma unroll
       for (int j = 0; j < kW4Deg; ++j) {
-        if (j < d) {
+        if (j < dd) {
           // beta_0 = B_1, beta_{d-1} = F_{d-2}, else the middle R_j
-          const uint2 r = j == 0 ? Bc : (j == d - 1 ? Flast : R[j]);
+          const uint2 r = j == 0 ? Bc : (j == dd - 1 ? Flast : R[j]);
           be[j] = __byte_perm(r.x, r.y, bsel[j]);
-          reinterpret_cast<uint32_t*>(X)[e0 + j] = be[j];
+          if (mine) reinterpret_cast<uint32_t*>(X)[e0 + j] = be[j];
         }
       }
       __syncwarp();
@@ -722,7 +726,7 @@ __device__ __forceinline__ bool decode_frame_warp4(const JobDesc& job, int frame
       if (decide_now) cw = 0;
 #pragma unroll
       for (int j = 0; j < kW4Deg; ++j) {
-        if (j < d) {
+        if (j < dd) {
           uint32_t t0, t1, b0, b1;
           unpack(gr[j], t0, t1);
           if (oe[j] >= 0) {
@@ -779,7 +783,7 @@ __device__ __forceinline__ void decode_frame(const JobDesc& job, int frame, uint
   static_assert(!PR || (g::G == 32 && MB == 1 && !T1), "pruned convolutions: 32-lane groups, 8-bit, minimal");
   if constexpr (Q == 4 && MB == 1 && !T1 && REG4 && W4) {
     // one warp per frame: a slot of 32 threads
-    if (nthr == 32 && decode_frame_warp4(job, frame, X, sblob, stid)) return;
+    if (nthr == 32 && decode_frame_warp4<D == 4 ? 4 : 0>(job, frame, X, sblob, stid)) return;
   }
   // pairs (x, y) the convolutions visit in this frame (counted when job.work is set)
   const bool counting = job.work != nullptr;

@@ -89,7 +89,9 @@ const void* kernel_for(int q, int v, int km, int dreg = 0) {
 }
 
 // the regular check degree that selects a specialised kernel (see kernel_for), else 0
-int kernel_dreg(int q, int v, int km, int dreg) { return (q == 64 && km == 1 && v >= 2 && v <= 3 && dreg == 4) ? 4 : 0; }
+int kernel_dreg(int q, int v, int km, int dreg) {
+  return ((q == 64 || q == 4) && km == 1 && v >= 2 && v <= 3 && dreg == 4) ? 4 : 0;
+}
 
 template <int Q> int lanes(int v) { return v ? nbldpc::Geo<Q, 1>::G : nbldpc::Geo<Q, 0>::G; }
 
@@ -123,14 +125,14 @@ int group_bytes(int q, int dmax, int mb) {
 
 // Every kernel may use up to the opt-in shared memory of the device (set once
 // per device and kernel; occupancy still follows the bytes of each launch).
-bool g_attr_done[64][83] = {};
+bool g_attr_done[64][85] = {};
 
 // per field order: 3 kernel modes x 2 layouts, the 2 resident-message kernels,
-// then the 2 pruned-convolution kernels; after them the 2 GF(64) resident kernels
-// of check degree 4
+// then the 2 pruned-convolution kernels; after them the 2 GF(64) and the 2 GF(4)
+// resident kernels of check degree 4
 int kernel_slot(int q, int v, int km, int dreg) {
   if (q == 0) return 0;
-  if (kernel_dreg(q, v, km, dreg)) return 81 + (v & 1);
+  if (kernel_dreg(q, v, km, dreg)) return (q == 64 ? 81 : 83) + (v & 1);
   return 1 + 10 * (nbldpc::ilog2(q) - 1) + ((v & 4) ? 8 + (v & 1) : (v & 2) ? 6 + (v & 1) : 2 * (km - 1) + (v & 1));
 }
 
