@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import gc
 import json
 import os
 import platform
@@ -713,6 +714,16 @@ def run_serving(args, ws, rank, local, emit=True, loads_c=(0.10, 0.25, 0.50, 0.7
         srv = Server(ex, budget_bytes=budget, streams=3, mode=mode)
         r = np.random.Generator(np.random.PCG64(seed))
         reqs = []
+        # no garbage-collector pause inside the window: the polling loop is what
+        # observes completions, so a pause would show up as request latency
+        gc.collect()
+        gc.disable()
+        try:
+            return window(srv, r, reqs, rate, seconds, saturate, cap)
+        finally:
+            gc.enable()
+
+    def window(srv, r, reqs, rate, seconds, saturate, cap):
         t0 = time.perf_counter()
         if saturate:
             for i in range(2 * len(pool)):
